@@ -1,0 +1,222 @@
+/*
+ * vsie.h - C ABI of libvsie, a GB300 (sm_103a) implementation of the hybrid
+ * volume-surface integral equation (hybrid-VSIE) matrix-vector product and the
+ * GMRES that applies it (Giannakopoulos et al., "A hybrid volume-surface
+ * integral equation method for rapid electromagnetic simulations in MRI").
+ *
+ * The system solved is Eq. (hvsie) of the paper,
+ *
+ *     [ Z_ff    Z_fn^T  Z_fb^T ] [ j_f ]   [ v_f ]
+ *     [ Z_fn    Z_nn    Z_nb^T ] [ j_n ] = [ v_n ]
+ *     [ Z_fb    Z_nb    Z_bb   ] [ j_b ]   [  0  ]
+ *
+ * in its compressed form Eq. (hvsie_disc): far conductors (shield, bore) j_f,
+ * near conductors (coils) j_n, body polarisation currents j_b.  Z_bb and the
+ * near block are applied by the precorrected FFT on an extended voxel grid
+ * (Sec. II.C, III), Z_fn by its ACA factors U V^H (Sec. III), the far coupling
+ * Z_fb by its tensor trains with Eq. (mvp) and Eq. (tmvp), and Z_ff densely.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Unknown vector of length N = m_f + m_n + 3 * n_b, ordered [j_f; j_n; j_b].
+ *    j_b is component-major: j_b[a * n_b + v], a in {x, y, z}, body voxel
+ *    v = i1 + n1 * (i2 + n2 * i3) (i1 fastest, the column-major order of
+ *    Eq. (mvp)).
+ *  - Complex numbers are interleaved (re, im): double2 for VSIE_C128, float2
+ *    for VSIE_C64.  Blocks of p right-hand sides are column-major with a
+ *    leading dimension (in complex elements) >= N.
+ *  - Voxels whose material has chi = eps_r - 1 - i sigma / (omega eps0) = 0
+ *    (vacuum) carry identity rows and columns: their output equals their input.
+ *  - Device pointers are owned by the caller (for example torch tensors); the
+ *    library never frees caller memory.  A context owns all its own device
+ *    allocations and frees them in vsie_destroy.
+ *  - Work is enqueued on the caller's stream and is asynchronous unless stated.
+ *  - A context is not thread-safe: use one per host thread and stream.
+ *  - No exceptions or aborts cross the ABI.  Every call returns a status; the
+ *    message of the last failure is returned by vsie_last_error.
+ */
+#ifndef VSIE_H
+#define VSIE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VSIE_API __attribute__((visibility("default")))
+#else
+#define VSIE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vsie_ctx vsie_ctx;
+typedef struct CUstream_st* vsie_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    VSIE_OK = 0,
+    VSIE_EINVAL = 1,       /* invalid argument (null pointer, size, mesh, grid) */
+    VSIE_ENOMEM = 2,       /* device or host allocation failed */
+    VSIE_ECUDA = 3,        /* a CUDA runtime call failed */
+    VSIE_ENOCONV = 4,      /* iterative solver hit maxit; X holds the last iterate */
+    VSIE_EBREAKDOWN = 5,   /* non-finite values met (NaN/Inf in data or iterate) */
+    VSIE_ETIMEOUT = 6,     /* a bounded device wait ran out */
+    VSIE_EUNSUPPORTED = 7  /* valid but unsupported request (e.g. FFT length) */
+} vsie_status;
+
+enum { VSIE_C128 = 0, VSIE_C64 = 1 };
+
+/* Uniform voxel grid: n[0] x n[1] x n[2] voxels of edge h (metres); voxel
+ * (0,0,0) is centred at origin. */
+typedef struct {
+    int32_t n[3];
+    double h;
+    double origin[3];
+} vsie_grid;
+
+/* Triangle mesh (metres): xyz[3*nverts], tri[3*ntris] (vertex ids),
+ * ports[2*nports] (vertex pairs naming interior port edges). */
+typedef struct {
+    int32_t nverts;
+    const double* xyz;
+    int32_t ntris;
+    const int32_t* tri;
+    int32_t nports;
+    const int32_t* ports;
+} vsie_mesh;
+
+/* Set-up options.  Zero-initialise and override; zeros select the defaults. */
+typedef struct {
+    int32_t ext_n[3];      /* extended pFFT grid (0 = the body grid)                    */
+    int32_t ext_offset[3]; /* body grid offset inside the extended grid                 */
+    int32_t stencil;       /* pFFT expansion stencil s (odd; default 3)                 */
+    int32_t near_radius;   /* precorrection radius in voxels (default s + 1)            */
+    double colloc_rfac;    /* collocation sphere radius = rfac * s * h / 2 (default 2)  */
+    double tt_tol;         /* TT tolerance of the far coupling (default 1e-6)           */
+    double aca_tol;        /* ACA tolerance of the near-far block (default 1e-6)        */
+    int32_t max_rhs;       /* largest p passed to vsie_matvec / vsie_solve (default 16) */
+    int32_t precisions;    /* bit mask (1 << VSIE_C128) | (1 << VSIE_C64); default both */
+} vsie_options;
+
+/* Compressed operator parts, for vsie_create.  All arrays are host memory,
+ * complex interleaved (double2), column-major unless stated.  Sizes:
+ *   W          [m_n][3 s^3]  projection weights of each near RWG, index
+ *                            b * s^3 + qx + s*(qy + s*qz) (row per RWG)
+ *   base       [m_n][3]      lowest-corner voxel (ext grid) of each stencil
+ *   pre_*      CSR of the precorrection (Z form) with 3 n_b rows (body unknowns)
+ *              and m_n columns: rowptr[3 n_b + 1], col[nnz], val[nnz]
+ *   Znn        m_n x m_n     near block with the grid part folded out
+ *   U, V       m_n x k, m_f x k   U V^H ~= Z_fn  (k = aca_rank, may be 0)
+ *   Zff        m_f x m_f
+ *   tt_rank    [3][3]        (r1, r2, r3) per component
+ *   tt_core    [3][4]        G1 (n1 x r1), G2 (r1 x n2 x r2), G3 (r2 x n3 x r3),
+ *                            G4 (r3 x m_f), column-major (first index fastest)
+ * m_n = 0 or m_f = 0 drop the corresponding blocks. */
+typedef struct {
+    int32_t m_f, m_n, stencil;
+    const double* W;
+    const int32_t* base;
+    int64_t pre_nnz;
+    const int64_t* pre_rowptr;
+    const int32_t* pre_col;
+    const double* pre_val;
+    const double* Znn;
+    int32_t aca_rank;
+    const double* U;
+    const double* V;
+    const double* Zff;
+    int32_t tt_rank[3][3];
+    const double* tt_core[3][4];
+} vsie_parts;
+
+/* Solver options for vsie_solve (zero-initialise; zeros select defaults). */
+typedef struct {
+    int32_t mode;       /* 0 = plain FP64 GMRES; 1 = FP32 inner FGMRES with FP64 refinement */
+    int32_t restart;    /* GMRES restart length m (default 50)                            */
+    int32_t maxit;      /* total inner iteration cap per RHS (default 2000)               */
+    double inner_tol;   /* mode 1: relative tolerance of each inner solve (default 1e-4)  */
+    int32_t max_outer;  /* mode 1: refinement steps cap (default 20)                      */
+} vsie_solve_opts;
+
+typedef struct {
+    int32_t iters[64];      /* inner iterations per RHS (first 64 RHS)                   */
+    double relres[64];      /* final true relative residual ||b - Z x|| / ||b|| (FP64)   */
+    int32_t outer;          /* refinement steps taken (mode 1)                           */
+    int32_t matvecs64;      /* FP64 operator applications                                 */
+    int32_t matvecs32;      /* FP32 operator applications                                 */
+    double seconds;         /* wall time of the solve                                     */
+} vsie_solve_info;
+
+/* Message of the last failure on ctx (or of the last failed context-less call
+ * when ctx is NULL).  The pointer stays valid until the next call. */
+VSIE_API const char* vsie_last_error(const vsie_ctx* ctx);
+
+/* Library version string. */
+VSIE_API const char* vsie_version(void);
+
+/* Full set-up from geometry (Sec. III): body grid and material maps
+ * (eps_r, sigma: n_b host doubles each, S/m), near conductors `coil` and far
+ * conductors `shield` (either may be NULL), frequency in Hz.  Builds RWG
+ * functions, the Green spectra of the extended grid, the pFFT projection and
+ * precorrection, the dense near block, the ACA factors of Z_fn, the dense Z_ff
+ * and the TT of Z_fb (ACA matrix cross over the (voxel | far RWG) unfolding,
+ * then TT-SVD of the voxel factor).  Synchronous; uses the current device.
+ * Returns EINVAL for malformed meshes/grids or stencils leaving the extended
+ * grid, ENOMEM/ECUDA on device failures.  *out is set only on success. */
+VSIE_API vsie_status vsie_setup(const vsie_grid* body, const double* eps_r, const double* sigma,
+                       const vsie_mesh* coil, const vsie_mesh* shield, double freq_hz,
+                       const vsie_options* opts, vsie_ctx** out);
+
+/* Create a context from precomputed compressed parts (for example loaded from
+ * disk, or produced by another implementation).  Same body/material/frequency
+ * meaning as vsie_setup; parts may be NULL (volume operator only).  The Green
+ * spectra are computed here.  Synchronous. */
+VSIE_API vsie_status vsie_create(const vsie_grid* body, const double* eps_r, const double* sigma,
+                        double freq_hz, const vsie_options* opts, const vsie_parts* parts,
+                        vsie_ctx** out);
+
+/* Sizes of the unknown vector. Any output pointer may be NULL. */
+VSIE_API vsie_status vsie_sizes(const vsie_ctx* ctx, int64_t* N, int64_t* m_f, int64_t* m_n,
+                       int64_t* n_b);
+
+/* Y = Z X for p right-hand sides (Eq. hvsie_disc).  X, Y: device pointers,
+ * column-major N x p with leading dimensions ldx, ldy (complex elements);
+ * precision VSIE_C128 (double2) or VSIE_C64 (float2).  X and Y must not
+ * overlap.  1 <= p <= opts.max_rhs.  Asynchronous on `stream`. */
+VSIE_API vsie_status vsie_matvec(vsie_ctx* ctx, int32_t p, const void* X, int64_t ldx, void* Y,
+                        int64_t ldy, int32_t precision, vsie_stream stream);
+
+/* Delta-gap right-hand sides i omega eps0 V l_m of the listed ports (indices
+ * into the concatenation [shield ports; coil ports]) into B (device, double2,
+ * column-major N x nports, leading dimension ldb), one column per port. */
+VSIE_API vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t* ports, double V,
+                           void* B, int64_t ldb, vsie_stream stream);
+
+/* Solve Z X = B for p right-hand sides to relative FP64 residual tol (Sec. III.A:
+ * GMRES with restart; x0 = 0).  B, X: device double2 (C128), column-major N x p.
+ * mode 0: every matvec, orthogonalisation and Givens update in FP64.
+ * mode 1: FP32 matvec inside flexible GMRES, FP64 outer residual r = B - Z X and
+ * FP64 Gram-Schmidt/Givens (iterative refinement).  Synchronous with respect to
+ * `stream`.  info (host) may be NULL.  Returns ENOCONV when any RHS misses tol
+ * (X then holds the last iterate and info its residual). */
+VSIE_API vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t ldb, void* X,
+                       int64_t ldx, double tol, const vsie_solve_opts* opts,
+                       vsie_solve_info* info, vsie_stream stream);
+
+/* Write the context's operator (grid, materials, frequency, options, parts) to
+ * a versioned binary file; vsie_load recreates a context from it (Sec. VI:
+ * compressed coupling matrices stored and reused). */
+VSIE_API vsie_status vsie_save(const vsie_ctx* ctx, const char* path);
+VSIE_API vsie_status vsie_load(const char* path, vsie_ctx** out);
+
+/* Copy the context's parts to host arrays owned by the context (valid until
+ * vsie_destroy); pointers in *parts refer to that storage. */
+VSIE_API vsie_status vsie_get_parts(vsie_ctx* ctx, vsie_parts* parts);
+
+VSIE_API void vsie_destroy(vsie_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSIE_H */

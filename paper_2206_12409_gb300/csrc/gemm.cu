@@ -1,0 +1,190 @@
+// Complex GEMM used by the surface blocks (K6: Z_ff, Znn, U V^H and conj(V) U^T)
+// and the TT chain (K5: Eq. mvp and Eq. tmvp are sequences of small-K
+// contractions).  Column-major; C_b = alpha op(A_b) B_b + beta C_b.
+// Tiles of BM x BN outputs, BK = 16 staged through shared memory; split-K
+// partial sums go to a workspace and are reduced in a fixed order (the result
+// does not depend on scheduling).  Optional masks: maskB zeroes B elements,
+// maskC leaves masked C elements untouched.
+#include "vsie_internal.h"
+
+namespace vsie {
+
+constexpr int BK = 16;
+
+template <typename R, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(256)
+k_cgemm(int opA, int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A, int64_t lda,
+        int64_t sA, const cx<R>* __restrict__ B, int64_t ldb, int64_t sB, cx<R> beta,
+        cx<R>* __restrict__ C, int64_t ldc, int64_t sC, int batch, int splits,
+        const uint8_t* __restrict__ maskB, const uint8_t* __restrict__ maskC,
+        cx<R>* __restrict__ ws) {
+    using Cx = cx<R>;
+    constexpr int TX = BM / TM, TY = BN / TN;
+    static_assert(TX * TY == 256, "256 threads");
+    __shared__ Cx As[BK][BM + 1];
+    __shared__ Cx Bs[BK][BN + 1];
+    const int bz = blockIdx.z;
+    const int b = bz % batch, sp = bz / batch;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const Cx* Ab = A + (size_t)b * sA;
+    const Cx* Bb = B + (size_t)b * sB;
+    const int ktiles = (K + BK - 1) / BK;
+    const int per = (ktiles + splits - 1) / splits;
+    const int kt0 = sp * per, kt1 = min(ktiles, kt0 + per);
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    Cx acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = czero<Cx>();
+    const bool trans = (opA == OP_T || opA == OP_H);
+    const bool conj = (opA == OP_H || opA == OP_R);
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int k0 = kt * BK;
+        for (int e = tid; e < BM * BK; e += 256) {
+            int m, k;
+            if (trans) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
+            const int gm = m0 + m, gk = k0 + k;
+            Cx v = czero<Cx>();
+            if (gm < M && gk < K) {
+                v = trans ? Ab[(size_t)gk + (size_t)gm * lda] : Ab[(size_t)gm + (size_t)gk * lda];
+                if (conj) v.y = -v.y;
+            }
+            As[k][m] = v;
+        }
+        for (int e = tid; e < BK * BN; e += 256) {
+            const int k = e % BK, n = e / BK;
+            const int gk = k0 + k, gn = n0 + n;
+            Cx v = czero<Cx>();
+            if (gk < K && gn < N) {
+                v = Bb[(size_t)gk + (size_t)gn * ldb];
+                if (maskB && !maskB[(size_t)gk + (size_t)K * gn]) v = czero<Cx>();
+            }
+            Bs[k][n] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            Cx a[TM], bb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[k][tx + i * TX];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[k][ty + j * TY];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+    if (splits > 1) {
+        Cx* w = ws + ((size_t)sp * batch + b) * (size_t)M * N;
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int gm = m0 + tx + i * TX, gn = n0 + ty + j * TY;
+                if (gm < M && gn < N) w[(size_t)gm + (size_t)M * gn] = acc[i][j];
+            }
+        return;
+    }
+    Cx* Cb = C + (size_t)b * sC;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int gm = m0 + tx + i * TX, gn = n0 + ty + j * TY;
+            if (gm >= M || gn >= N) continue;
+            if (maskC && !maskC[(size_t)gm + (size_t)M * gn]) continue;
+            Cx* cp = Cb + (size_t)gm + (size_t)gn * ldc;
+            Cx r = cmul(alpha, acc[i][j]);
+            if (beta.x != 0 || beta.y != 0) cfma(r, beta, *cp);
+            *cp = r;
+        }
+}
+
+template <typename R>
+__global__ void k_splitk_reduce(int M, int N, int batch, int splits, cx<R> alpha,
+                                const cx<R>* __restrict__ ws, cx<R> beta, cx<R>* __restrict__ C,
+                                int64_t ldc, int64_t sC, const uint8_t* __restrict__ maskC) {
+    using Cx = cx<R>;
+    const size_t tot = (size_t)batch * M * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int b = e / ((size_t)M * N);
+        const size_t r = e - (size_t)b * M * N;
+        const int gm = r % M, gn = r / M;
+        if (maskC && !maskC[(size_t)gm + (size_t)M * gn]) continue;
+        Cx s = czero<Cx>();
+        for (int sp = 0; sp < splits; ++sp) s = cadd(s, ws[((size_t)sp * batch + b) * M * N + r]);
+        Cx* cp = C + (size_t)b * sC + gm + (size_t)gn * ldc;
+        Cx out = cmul(alpha, s);
+        if (beta.x != 0 || beta.y != 0) cfma(out, beta, *cp);
+        *cp = out;
+    }
+}
+
+template <typename R, int BM, int BN, int TM, int TN>
+static void launch(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+                   int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
+                   cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
+                   const uint8_t* maskC, cudaStream_t st) {
+    OpData<R>& d = data<R>(c);
+    const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+    const int ktiles = (K + BK - 1) / BK;
+    const long tiles = (long)tm * tn * batch;
+    int splits = 1;
+    if (tiles < 2 * 152 && ktiles >= 8) {
+        splits = (int)((2 * 152 + tiles - 1) / tiles);
+        splits = std::min(splits, ktiles / 4);
+        splits = std::max(splits, 1);
+        const size_t need = (size_t)splits * batch * M * N;
+        while (splits > 1 && need > d.splitk_elems) {
+            --splits;
+        }
+        if ((size_t)splits * batch * M * N > d.splitk_elems) splits = 1;
+    }
+    dim3 g(tm, tn, batch * splits);
+    k_cgemm<R, BM, BN, TM, TN><<<g, 256, 0, st>>>(opA, M, N, K, alpha, A, lda, sA, B, ldb, sB,
+                                                  beta, C, ldc, sC, batch, splits, maskB, maskC,
+                                                  d.splitk);
+    if (splits > 1) {
+        const size_t tot = (size_t)batch * M * N;
+        const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+        k_splitk_reduce<R><<<blocks, 256, 0, st>>>(M, N, batch, splits, alpha, d.splitk, beta, C,
+                                                   ldc, sC, maskC);
+    }
+    VSIE_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void cgemm(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const cx<R>* A, int64_t lda,
+           int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
+           int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
+           cudaStream_t st) {
+    if (M <= 0 || N <= 0 || batch <= 0) return;
+    if (K <= 0) {
+        // C = beta C
+        if (beta.x == 1 && beta.y == 0) return;
+    }
+    if (N <= 8)
+        launch<R, 128, 8, 4, 1>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                batch, maskB, maskC, st);
+    else if (N <= 16)
+        launch<R, 64, 16, 2, 2>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                batch, maskB, maskC, st);
+    else
+        launch<R, 64, 64, 4, 4>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                batch, maskB, maskC, st);
+}
+
+template void cgemm<float>(Ctx&, GemmOp, int, int, int, float2, const float2*, int64_t, int64_t,
+                           const float2*, int64_t, int64_t, float2, float2*, int64_t, int64_t,
+                           int, const uint8_t*, const uint8_t*, cudaStream_t);
+template void cgemm<double>(Ctx&, GemmOp, int, int, int, double2, const double2*, int64_t,
+                            int64_t, const double2*, int64_t, int64_t, double2, double2*,
+                            int64_t, int64_t, int, const uint8_t*, const uint8_t*,
+                            cudaStream_t);
+
+}  // namespace vsie

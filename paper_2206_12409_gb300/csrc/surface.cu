@@ -1,0 +1,168 @@
+// Surface blocks of the hybrid-VSIE matvec (Eq. hvsie_disc):
+//   K2  pFFT projection (P x_n onto the coil-active voxels of the extended grid),
+//       gather form: one output per (active voxel, component, RHS), no atomics;
+//   K3  pFFT interpolation y_n = -P^T c (c: convolution on active voxels);
+//   K4  precorrection y_b += Pre x_n and y_n += Pre^T (M x_b) (two CSR forms);
+//   K6  y_n += Znn x_n + U (V^H x_f),  y_f = Z_ff x_f + conj(V) (U^T x_n);
+//   K5  y_b += M TT(x_f) by Eq. (mvp), y_f += sum_chi TT_chi^T (M x_b,chi) by
+//       Eq. (tmvp), each a chain of contractions (cgemm).
+#include "vsie_internal.h"
+
+namespace vsie {
+
+template <typename R>
+__global__ void k_scatter(int64_t nrows, int p, const int32_t* __restrict__ ptr,
+                          const int32_t* __restrict__ col, const cx<R>* __restrict__ val,
+                          const cx<R>* __restrict__ X, int64_t ldx, int64_t xoff,
+                          cx<R>* __restrict__ gc) {
+    // rows are (b, c) = b * nact + c; output gc[(j * 3 + b) * nact + c] = gc[j * nrows + row]
+    const int64_t tot = nrows * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e % nrows;
+        const int j = e / nrows;
+        const cx<R>* x = X + (size_t)j * ldx + xoff;
+        cx<R> s = czero<cx<R>>();
+        for (int q = ptr[row]; q < ptr[row + 1]; ++q) cfma(s, val[q], x[col[q]]);
+        gc[(size_t)j * nrows + row] = s;
+    }
+}
+
+template <typename R>
+__global__ void k_gather(int m_n, int p, int s3, int64_t nact, const cx<R>* __restrict__ W,
+                         const int32_t* __restrict__ cidx, const cx<R>* __restrict__ cc,
+                         cx<R>* __restrict__ Y, int64_t ldy, int64_t yoff) {
+    const int64_t tot = (int64_t)m_n * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int n = e % m_n;
+        const int j = e / m_n;
+        cx<R> s = czero<cx<R>>();
+        for (int b = 0; b < 3; ++b) {
+            const cx<R>* cb = cc + ((size_t)j * 3 + b) * nact;
+            const cx<R>* w = W + (size_t)n * 3 * s3 + b * s3;
+            const int32_t* ci = cidx + (size_t)n * s3;
+            for (int q = 0; q < s3; ++q) cfma(s, w[q], cb[ci[q]]);
+        }
+        Y[(size_t)j * ldy + yoff + n] = make_neg(s);
+    }
+}
+
+// Row-compressed CSR SpMV: y[rows[r]] += sum val * x[col]; optional row mask
+// (rows of vacuum voxels are left untouched) and optional column mask.
+template <typename R>
+__global__ void k_spmv_add(int64_t nr, int p, const int32_t* __restrict__ rows,
+                           const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const cx<R>* __restrict__ val, const cx<R>* __restrict__ X,
+                           int64_t ldx, int64_t xoff, cx<R>* __restrict__ Y, int64_t ldy,
+                           int64_t yoff, const uint8_t* __restrict__ rowmask, int64_t rowmod,
+                           const uint8_t* __restrict__ colmask, int64_t colmod) {
+    const int64_t tot = nr * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % nr;
+        const int j = e / nr;
+        const int64_t row = rows[r];
+        if (rowmask && !rowmask[row % rowmod]) continue;
+        const cx<R>* x = X + (size_t)j * ldx + xoff;
+        cx<R> s = czero<cx<R>>();
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) {
+            const int32_t cidx = col[q];
+            if (colmask && !colmask[cidx % colmod]) continue;
+            cfma(s, val[q], x[cidx]);
+        }
+        cx<R>* y = Y + (size_t)j * ldy + yoff + row;
+        *y = cadd(*y, s);
+    }
+}
+
+static inline int nblk(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+template <typename R>
+void surface_pre(Ctx& c, int p, const cx<R>* X, int64_t ldx, cudaStream_t st) {
+    OpData<R>& d = data<R>(c);
+    if (c.m_n == 0 || c.nact == 0) return;
+    const int64_t nrows = 3 * c.nact;
+    k_scatter<R><<<nblk(nrows * p), 256, 0, st>>>(nrows, p, c.sc_ptr, c.sc_col, d.sc_val, X, ldx,
+                                                  (int64_t)c.m_f, d.gc);
+    VSIE_CUDA(cudaGetLastError());
+}
+
+template <typename R>
+void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                   cudaStream_t st) {
+    using C = cx<R>;
+    OpData<R>& d = data<R>(c);
+    const C one = mk<C>(1, 0), zero = mk<C>(0, 0);
+    const int64_t xb = (int64_t)c.m_f + c.m_n;
+    const int mf = c.m_f, mn = c.m_n;
+    if (mn > 0) {
+        const int s3 = c.s * c.s * c.s;
+        k_gather<R><<<nblk((int64_t)mn * p), 256, 0, st>>>(mn, p, s3, c.nact, d.W, c.W_cidx, d.cc,
+                                                           Y, ldy, (int64_t)mf);
+        VSIE_CUDA(cudaGetLastError());
+        cgemm<R>(c, OP_N, mn, p, mn, one, d.Znn, mn, 0, X + mf, ldx, 0, one, Y + mf, ldy, 0, 1,
+                 nullptr, nullptr, st);
+        if (c.pre_nnz > 0) {
+            k_spmv_add<R><<<nblk(c.pre_nr * p), 256, 0, st>>>(
+                c.pre_nr, p, c.pre_rows, c.pre_ptr, c.pre_col, d.pre_val, X, ldx, (int64_t)mf, Y,
+                ldy, xb, c.mask, c.n_b, nullptr, 1);
+            k_spmv_add<R><<<nblk(c.preT_nr * p), 256, 0, st>>>(
+                c.preT_nr, p, c.preT_rows, c.preT_ptr, c.preT_col, d.preT_val, X, ldx, xb, Y, ldy,
+                (int64_t)mf, nullptr, 1, c.mask, c.n_b);
+            VSIE_CUDA(cudaGetLastError());
+        }
+    }
+    if (mf > 0) {
+        cgemm<R>(c, OP_N, mf, p, mf, one, d.Zff, mf, 0, X, ldx, 0, zero, Y, ldy, 0, 1, nullptr,
+                 nullptr, st);
+        if (mn > 0 && c.aca_rank > 0) {
+            const int k = c.aca_rank;
+            // t = V^H x_f (k x p); y_n += U t
+            cgemm<R>(c, OP_H, k, p, mf, one, d.V, mf, 0, X, ldx, 0, zero, d.t1, k, 0, 1, nullptr,
+                     nullptr, st);
+            cgemm<R>(c, OP_N, mn, p, k, one, d.U, mn, 0, d.t1, k, 0, one, Y + mf, ldy, 0, 1,
+                     nullptr, nullptr, st);
+            // t = U^T x_n; y_f += conj(V) t
+            cgemm<R>(c, OP_T, k, p, mn, one, d.U, mn, 0, X + mf, ldx, 0, zero, d.t1, k, 0, 1,
+                     nullptr, nullptr, st);
+            cgemm<R>(c, OP_R, mf, p, k, one, d.V, mf, 0, d.t1, k, 0, one, Y, ldy, 0, 1, nullptr,
+                     nullptr, st);
+        }
+        // tensor trains of the far coupling, one per component
+        const int n1 = c.nb[0], n2 = c.nb[1], n3 = c.nb[2];
+        for (int a = 0; a < 3; ++a) {
+            const int r1 = c.tt_rank[a][0], r2 = c.tt_rank[a][1], r3 = c.tt_rank[a][2];
+            if (r1 == 0) continue;
+            C* const* G = d.G[a];
+            const int64_t boff = xb + (int64_t)a * c.n_b;
+            // Eq. (mvp): y = G4 x_f; y = G3 y; Y = G2 Y; Y = G1 Y (masked accumulate)
+            cgemm<R>(c, OP_T, r3, p, mf, one, G[3], mf, 0, X, ldx, 0, zero, d.t1, r3, 0, 1,
+                     nullptr, nullptr, st);
+            cgemm<R>(c, OP_N, r2 * n3, p, r3, one, G[2], (int64_t)r2 * n3, 0, d.t1, r3, 0, zero,
+                     d.t2, (int64_t)r2 * n3, 0, 1, nullptr, nullptr, st);
+            cgemm<R>(c, OP_N, r1 * n2, n3 * p, r2, one, G[1], (int64_t)r1 * n2, 0, d.t2, r2, 0,
+                     zero, d.t3, (int64_t)r1 * n2, 0, 1, nullptr, nullptr, st);
+            cgemm<R>(c, OP_N, n1, n2 * n3, r1, one, G[0], n1, 0, d.t3, r1,
+                     (int64_t)r1 * n2 * n3, one, Y + boff, n1, ldy, p, nullptr, c.mask, st);
+            // Eq. (tmvp): Z1 = G1^T (M x_b); Z2 = G2^T Z1; Z3 = G3^T Z2; y_f += G4^T Z3
+            cgemm<R>(c, OP_T, r1, n2 * n3, n1, one, G[0], n1, 0, X + boff, n1, ldx, zero, d.t3,
+                     r1, (int64_t)r1 * n2 * n3, p, c.mask, nullptr, st);
+            cgemm<R>(c, OP_T, r2, n3 * p, r1 * n2, one, G[1], (int64_t)r1 * n2, 0, d.t3,
+                     (int64_t)r1 * n2, 0, zero, d.t2, r2, 0, 1, nullptr, nullptr, st);
+            cgemm<R>(c, OP_T, r3, p, r2 * n3, one, G[2], (int64_t)r2 * n3, 0, d.t2,
+                     (int64_t)r2 * n3, 0, zero, d.t1, r3, 0, 1, nullptr, nullptr, st);
+            cgemm<R>(c, OP_N, mf, p, r3, one, G[3], mf, 0, d.t1, r3, 0, one, Y, ldy, 0, 1, nullptr,
+                     nullptr, st);
+        }
+    }
+}
+
+template void surface_pre<float>(Ctx&, int, const float2*, int64_t, cudaStream_t);
+template void surface_pre<double>(Ctx&, int, const double2*, int64_t, cudaStream_t);
+template void surface_apply<float>(Ctx&, int, const float2*, int64_t, float2*, int64_t,
+                                   cudaStream_t);
+template void surface_apply<double>(Ctx&, int, const double2*, int64_t, double2*, int64_t,
+                                    cudaStream_t);
+
+}  // namespace vsie

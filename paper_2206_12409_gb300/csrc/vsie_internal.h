@@ -1,0 +1,227 @@
+// Internal declarations of libvsie (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <complex>
+
+#include "../../include/vsie.h"
+
+namespace vsie {
+
+template <int N> struct int_ {};
+
+// ----------------------------------------------------------------- complex math
+template <typename R> struct cx_of;
+template <> struct cx_of<float> { using type = float2; };
+template <> struct cx_of<double> { using type = double2; };
+template <typename R> using cx = typename cx_of<R>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im) {
+    C c; c.x = re; c.y = im; return c;
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C czero() { C c; c.x = 0; c.y = 0; return c; }
+template <typename C> __host__ __device__ __forceinline__ C make_neg(C a) { a.x = -a.x; a.y = -a.y; return a; }
+
+// Convert between precisions (device and host).
+__host__ __device__ __forceinline__ float2 to_c(float2 a, float2*) { return a; }
+__host__ __device__ __forceinline__ double2 to_c(double2 a, double2*) { return a; }
+__host__ __device__ __forceinline__ float2 to_c(double2 a, float2*) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ double2 to_c(float2 a, double2*) { return make_double2(a.x, a.y); }
+
+// ----------------------------------------------------------------- FFT plans
+constexpr int kMaxStages = 16;
+constexpr double kEps0 = 8.8541878128e-12;   // F/m (CODATA 2018)
+constexpr double kC0 = 299792458.0;          // m/s
+
+// One 1D FFT length: radix sequence (first stage first) and twiddle table
+// tw[m] = exp(-2 pi i m / L), m in [0, L), in both precisions.
+struct FFTPlan {
+    int L = 0;
+    int nst = 0;
+    int rad[kMaxStages] = {0};
+};
+
+bool fft_factor(int L, FFTPlan& plan);     // radices 8,4,2,3,5,7; false if L not 7-smooth
+int next_smooth(int n);                    // smallest 7-smooth integer >= n
+
+// ----------------------------------------------------------------- device buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-precision device data of the operator.
+template <typename R>
+struct OpData {
+    // volume / pFFT
+    cx<R>* spec = nullptr;      // 6 octant spectra, scaled by h^3 / (L1 L2 L3)
+    cx<R>* tw[3] = {nullptr, nullptr, nullptr};   // twiddles per axis
+    cx<R>* dinv = nullptr;      // h^3 / chi per body voxel (0 on vacuum)
+    cx<R>* W = nullptr;         // m_n x 3 s^3 projection weights (row per RWG)
+    cx<R>* sc_val = nullptr;    // scatter CSR values (active voxel-component rows)
+    cx<R>* pre_val = nullptr;   // precorrection CSR (body rows)
+    cx<R>* preT_val = nullptr;  // transposed precorrection CSR (RWG rows)
+    cx<R>* Znn = nullptr;
+    cx<R>* U = nullptr;
+    cx<R>* V = nullptr;
+    cx<R>* Zff = nullptr;
+    cx<R>* G[3][4] = {{nullptr}};   // TT cores; G[c][3] stored transposed (m_f x r3)
+    // workspaces
+    cx<R>* bufA = nullptr;      // [p][3][n3][n2][L1]
+    cx<R>* bufB = nullptr;      // [p][3][n3][L2][L1]
+    cx<R>* gc = nullptr;        // [p][3][nact] coil contributions on active voxels
+    cx<R>* cc = nullptr;        // [p][3][nact] convolution on active voxels
+    cx<R>* t1 = nullptr;        // small GEMM intermediates
+    cx<R>* t2 = nullptr;
+    cx<R>* t3 = nullptr;
+    cx<R>* t4 = nullptr;
+    cx<R>* splitk = nullptr;    // split-K partial sums
+    size_t splitk_elems = 0;
+    bool ready = false;
+};
+
+struct Ctx {
+    std::string err;
+    int device = 0;
+    // problem
+    int nb[3] = {0, 0, 0};      // body grid
+    int ne[3] = {0, 0, 0};      // extended grid
+    int off[3] = {0, 0, 0};     // body offset inside ext
+    double h = 0, origin[3] = {0, 0, 0};
+    double freq = 0, omega = 0, k0 = 0;
+    int64_t n_b = 0, n_e = 0;
+    int m_f = 0, m_n = 0, s = 3;
+    int64_t N = 0;
+    int max_rhs = 16;
+    int precisions = 3;
+    vsie_options opts{};
+    FFTPlan plan[3];
+    int L[3] = {0, 0, 0}, Lh[3] = {0, 0, 0};   // FFT lengths and octant sizes (L/2 + 1)
+    // host copies (for save / get_parts / setup bookkeeping)
+    std::vector<double> eps_r, sigma;
+    std::vector<std::complex<double>> hW, hPreVal, hZnn, hU, hV, hZff, hTT[3][4];
+    std::vector<int32_t> hBase, hPreCol;
+    std::vector<int64_t> hPreRow;
+    std::vector<std::complex<double>> hPreValRows, hPreValT;   // compressed-row orders
+    std::vector<int64_t> sc_src;       // scatter CSR entry -> index into hW
+    int aca_rank = 0;
+    int tt_rank[3][3] = {{0}};
+    std::vector<double> port_len;      // per port: edge length (far ports first)
+    std::vector<int64_t> port_row;     // per port: unknown index
+    // device index structures (precision independent)
+    uint8_t* mask = nullptr;           // n_b material flags
+    int32_t* line_ptr = nullptr;       // per ext line (i2,i3): CSR of active voxels
+    int32_t* line_i1 = nullptr;        // active entries: i1 within the line
+    int32_t* line_cidx = nullptr;      // active entries: compact index
+    int64_t nact = 0;                  // number of active voxels
+    int32_t* sc_ptr = nullptr;         // scatter CSR rows: 3 * nact + 1
+    int32_t* sc_col = nullptr;         // scatter CSR columns (RWG index)
+    int64_t sc_nnz = 0;
+    int32_t* W_cidx = nullptr;         // m_n x s^3 compact index of each stencil voxel
+    // precorrection, row-compressed CSR (only rows with entries)
+    int64_t pre_nr = 0;                // non-empty body-unknown rows
+    int32_t* pre_rows = nullptr;       // their indices a * n_b + v
+    int64_t* pre_ptr = nullptr;        // pre_nr + 1
+    int32_t* pre_col = nullptr;        // RWG index
+    int64_t pre_nnz = 0;
+    int64_t preT_nr = 0;               // transposed form: rows are RWG indices
+    int32_t* preT_rows = nullptr;
+    int64_t* preT_ptr = nullptr;
+    int32_t* preT_col = nullptr;       // body unknown index (a * n_b + v)
+    int32_t* body_lines = nullptr;     // flags per ext line: 1 body, 2 active, 3 both
+    OpData<float> f32;
+    OpData<double> f64;
+    std::vector<void*> allocs;         // every device allocation (freed at destroy)
+    // solver scratch (FP64)
+    double2* kr_V = nullptr;           // Krylov basis
+    double2* kr_Z = nullptr;           // flexible directions (FP32 stored as float2)
+    size_t kr_bytes = 0;
+    bool owns_all = true;
+};
+
+template <typename R> OpData<R>& data(Ctx& c);
+template <> inline OpData<float>& data<float>(Ctx& c) { return c.f32; }
+template <> inline OpData<double>& data<double>(Ctx& c) { return c.f64; }
+
+// ----------------------------------------------------------------- helpers
+#define VSIE_CUDA(call)                                                            \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            throw ::vsie::Error(VSIE_ECUDA, std::string(#call) + ": " +            \
+                                cudaGetErrorString(e_));                           \
+        }                                                                          \
+    } while (0)
+
+struct Error {
+    vsie_status st;
+    std::string msg;
+    Error(vsie_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+void* dalloc(Ctx& c, size_t bytes);  // cudaMalloc tracked in c.allocs, throws ENOMEM
+
+// launchers (defined in conv.cu / surface.cu)
+template <typename R>
+void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                cudaStream_t st);
+template <typename R>
+void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                   cudaStream_t st);
+template <typename R>
+void surface_pre(Ctx& c, int p, const cx<R>* X, int64_t ldx, cudaStream_t st);
+template <typename R>
+void conv_set_attrs();
+template <typename R>
+void upload_twiddles(Ctx& c);
+
+enum GemmOp { OP_N = 0, OP_T = 1, OP_H = 2, OP_R = 3 };  // R = conj, no transpose
+
+// C_b = alpha * op(A_b) * B_b + beta * C_b, b in [0, batch); optional masks:
+// maskB[k + K * n] gates B elements (zero when 0), maskC[m + M * n] gates the
+// update of C elements.  Column-major, complex.
+template <typename R>
+void cgemm(Ctx& c, GemmOp opA, int M, int Nn, int K, cx<R> alpha, const cx<R>* A, int64_t lda,
+           int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
+           int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
+           cudaStream_t st);
+
+// volume spectra set-up (green.cu)
+template <typename R>
+void build_spectra(Ctx& c);
+
+}  // namespace vsie

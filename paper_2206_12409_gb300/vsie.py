@@ -1,0 +1,287 @@
+"""ctypes binding of libvsie (include/vsie.h): argument marshalling only.
+
+Function names match the C ABI.  Device buffers are passed as integer device
+pointers (for example ``tensor.data_ptr()``) with leading dimensions in complex
+elements; streams as integer ``cudaStream_t`` handles (0 = default stream).
+Every computation runs inside libvsie; when the library cannot be loaded the
+calls raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvsie.so")
+
+VSIE_OK, VSIE_EINVAL, VSIE_ENOMEM, VSIE_ECUDA, VSIE_ENOCONV, VSIE_EBREAKDOWN, \
+    VSIE_ETIMEOUT, VSIE_EUNSUPPORTED = range(8)
+VSIE_C128, VSIE_C64 = 0, 1
+STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA",
+                4: "VSIE_ENOCONV", 5: "VSIE_EBREAKDOWN", 6: "VSIE_ETIMEOUT",
+                7: "VSIE_EUNSUPPORTED"}
+
+EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
+           "vsie_matvec", "vsie_rhs_ports", "vsie_solve", "vsie_save", "vsie_load",
+           "vsie_get_parts", "vsie_destroy"]
+
+
+class VsieError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vsie_grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("origin", C.c_double * 3)]
+
+
+class vsie_mesh(C.Structure):
+    _fields_ = [("nverts", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("ntris", C.c_int32),
+                ("tri", C.POINTER(C.c_int32)), ("nports", C.c_int32),
+                ("ports", C.POINTER(C.c_int32))]
+
+
+class vsie_options(C.Structure):
+    _fields_ = [("ext_n", C.c_int32 * 3), ("ext_offset", C.c_int32 * 3), ("stencil", C.c_int32),
+                ("near_radius", C.c_int32), ("colloc_rfac", C.c_double), ("tt_tol", C.c_double),
+                ("aca_tol", C.c_double), ("max_rhs", C.c_int32), ("precisions", C.c_int32)]
+
+
+class vsie_parts(C.Structure):
+    _fields_ = [("m_f", C.c_int32), ("m_n", C.c_int32), ("stencil", C.c_int32),
+                ("W", C.c_void_p), ("base", C.c_void_p), ("pre_nnz", C.c_int64),
+                ("pre_rowptr", C.c_void_p), ("pre_col", C.c_void_p), ("pre_val", C.c_void_p),
+                ("Znn", C.c_void_p), ("aca_rank", C.c_int32), ("U", C.c_void_p),
+                ("V", C.c_void_p), ("Zff", C.c_void_p), ("tt_rank", (C.c_int32 * 3) * 3),
+                ("tt_core", (C.c_void_p * 4) * 3)]
+
+
+class vsie_solve_opts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+
+
+class vsie_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int32 * 64), ("relres", C.c_double * 64), ("outer", C.c_int32),
+                ("matvecs64", C.c_int32), ("matvecs32", C.c_int32), ("seconds", C.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libvsie (built in-tree by paper_2206_12409_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvsie not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.vsie_last_error.restype = C.c_char_p
+    lib.vsie_last_error.argtypes = [P]
+    lib.vsie_version.restype = C.c_char_p
+    lib.vsie_version.argtypes = []
+    lib.vsie_setup.restype = C.c_int
+    lib.vsie_setup.argtypes = [C.POINTER(vsie_grid), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(vsie_mesh), C.POINTER(vsie_mesh), C.c_double,
+                               C.POINTER(vsie_options), C.POINTER(P)]
+    lib.vsie_create.restype = C.c_int
+    lib.vsie_create.argtypes = [C.POINTER(vsie_grid), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.c_double, C.POINTER(vsie_options),
+                                C.POINTER(vsie_parts), C.POINTER(P)]
+    lib.vsie_sizes.restype = C.c_int
+    lib.vsie_sizes.argtypes = [P] + [C.POINTER(C.c_int64)] * 4
+    lib.vsie_matvec.restype = C.c_int
+    lib.vsie_matvec.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
+    lib.vsie_rhs_ports.restype = C.c_int
+    lib.vsie_rhs_ports.argtypes = [P, C.c_int32, C.POINTER(C.c_int32), C.c_double, P, C.c_int64, P]
+    lib.vsie_solve.restype = C.c_int
+    lib.vsie_solve.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_double,
+                               C.POINTER(vsie_solve_opts), C.POINTER(vsie_solve_info), P]
+    lib.vsie_save.restype = C.c_int
+    lib.vsie_save.argtypes = [P, C.c_char_p]
+    lib.vsie_load.restype = C.c_int
+    lib.vsie_load.argtypes = [C.c_char_p, C.POINTER(P)]
+    lib.vsie_get_parts.restype = C.c_int
+    lib.vsie_get_parts.argtypes = [P, C.POINTER(vsie_parts)]
+    lib.vsie_destroy.restype = None
+    lib.vsie_destroy.argtypes = [P]
+    _lib = lib
+    return lib
+
+
+def _check(st, ctx=None):
+    if st != VSIE_OK:
+        lib = load_library()
+        msg = lib.vsie_last_error(ctx)
+        raise VsieError(st, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return C.cast(a.ctypes.data, C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return C.cast(a.ctypes.data, C.POINTER(C.c_int32))
+
+
+def make_grid(n, h, origin):
+    g = vsie_grid()
+    for i in range(3):
+        g.n[i] = int(n[i])
+        g.origin[i] = float(origin[i])
+    g.h = float(h)
+    return g
+
+
+def make_mesh(xyz, tri, ports=None):
+    """vsie_mesh over numpy arrays; returns (struct, keep-alive tuple)."""
+    xyz = np.ascontiguousarray(xyz, np.float64)
+    tri = np.ascontiguousarray(tri, np.int32)
+    ports = np.ascontiguousarray(np.zeros((0, 2)) if ports is None else ports, np.int32)
+    m = vsie_mesh(xyz.shape[0], _dptr(xyz), tri.shape[0], _iptr(tri), ports.shape[0], _iptr(ports))
+    return m, (xyz, tri, ports)
+
+
+def make_options(ext_n=None, ext_offset=None, stencil=0, near_radius=0, colloc_rfac=0.0,
+                 tt_tol=0.0, aca_tol=0.0, max_rhs=0, precisions=0):
+    o = vsie_options()
+    for i in range(3):
+        o.ext_n[i] = int(ext_n[i]) if ext_n is not None else 0
+        o.ext_offset[i] = int(ext_offset[i]) if ext_offset is not None else 0
+    o.stencil, o.near_radius, o.colloc_rfac = int(stencil), int(near_radius), float(colloc_rfac)
+    o.tt_tol, o.aca_tol, o.max_rhs, o.precisions = float(tt_tol), float(aca_tol), int(max_rhs), \
+        int(precisions)
+    return o
+
+
+def make_parts(m_f=0, m_n=0, stencil=3, W=None, base=None, pre_rowptr=None, pre_col=None,
+               pre_val=None, Znn=None, U=None, V=None, Zff=None, tt=None):
+    """vsie_parts over numpy arrays (complex arrays as complex128, column-major
+    matrices, TT cores per component as [G1, G2, G3, G4]); returns (struct,
+    keep-alive list)."""
+    keep = []
+
+    def cplx(a, order="F"):
+        a = np.asarray(a, np.complex128)
+        a = np.asfortranarray(a) if order == "F" else np.ascontiguousarray(a)
+        keep.append(a)
+        return C.c_void_p(a.ctypes.data)
+
+    p = vsie_parts()
+    p.m_f, p.m_n, p.stencil = int(m_f), int(m_n), int(stencil)
+    if m_n:
+        p.W = cplx(W, "C")
+        b = np.ascontiguousarray(base, np.int32)
+        keep.append(b)
+        p.base = C.c_void_p(b.ctypes.data)
+        p.Znn = cplx(Znn)
+        if pre_val is not None and len(pre_val):
+            rp = np.ascontiguousarray(pre_rowptr, np.int64)
+            pc = np.ascontiguousarray(pre_col, np.int32)
+            keep += [rp, pc]
+            p.pre_nnz = int(len(pre_val))
+            p.pre_rowptr = C.c_void_p(rp.ctypes.data)
+            p.pre_col = C.c_void_p(pc.ctypes.data)
+            p.pre_val = cplx(pre_val, "C")
+    if m_f:
+        p.Zff = cplx(Zff)
+        if U is not None and U.shape[1] > 0 and m_n:
+            p.aca_rank = int(U.shape[1])
+            p.U = cplx(U)
+            p.V = cplx(V)
+        if tt is not None:
+            for a in range(3):
+                G1, G2, G3, G4 = tt[a]
+                p.tt_rank[a][0], p.tt_rank[a][1], p.tt_rank[a][2] = \
+                    int(G1.shape[1]), int(G2.shape[2]), int(G3.shape[2])
+                for q, G in enumerate((G1, G2, G3, G4)):
+                    p.tt_core[a][q] = cplx(G)
+    return p, keep
+
+
+def vsie_version():
+    return load_library().vsie_version().decode()
+
+
+def vsie_setup(grid, eps_r, sigma, coil, shield, freq_hz, opts=None):
+    lib = load_library()
+    er = np.ascontiguousarray(eps_r, np.float64)
+    sg = np.ascontiguousarray(sigma, np.float64)
+    out = C.c_void_p()
+    st = lib.vsie_setup(C.byref(grid), _dptr(er), _dptr(sg),
+                        C.byref(coil) if coil is not None else None,
+                        C.byref(shield) if shield is not None else None, float(freq_hz),
+                        C.byref(opts) if opts is not None else None, C.byref(out))
+    _check(st)
+    return out
+
+
+def vsie_create(grid, eps_r, sigma, freq_hz, opts=None, parts=None):
+    lib = load_library()
+    er = np.ascontiguousarray(eps_r, np.float64)
+    sg = np.ascontiguousarray(sigma, np.float64)
+    out = C.c_void_p()
+    st = lib.vsie_create(C.byref(grid), _dptr(er), _dptr(sg), float(freq_hz),
+                         C.byref(opts) if opts is not None else None,
+                         C.byref(parts) if parts is not None else None, C.byref(out))
+    _check(st)
+    return out
+
+
+def vsie_sizes(ctx):
+    lib = load_library()
+    v = [C.c_int64() for _ in range(4)]
+    _check(lib.vsie_sizes(ctx, *[C.byref(x) for x in v]), ctx)
+    return tuple(int(x.value) for x in v)
+
+
+def vsie_matvec(ctx, p, X, ldx, Y, ldy, precision, stream=0):
+    lib = load_library()
+    _check(lib.vsie_matvec(ctx, int(p), C.c_void_p(int(X)), int(ldx), C.c_void_p(int(Y)),
+                           int(ldy), int(precision), C.c_void_p(int(stream))), ctx)
+
+
+def vsie_rhs_ports(ctx, ports, V, B, ldb, stream=0):
+    lib = load_library()
+    pr = (C.c_int32 * len(ports))(*[int(x) for x in ports])
+    _check(lib.vsie_rhs_ports(ctx, len(ports), pr, float(V), C.c_void_p(int(B)), int(ldb),
+                              C.c_void_p(int(stream))), ctx)
+
+
+def vsie_solve(ctx, p, B, ldb, X, ldx, tol, opts=None, stream=0, check=True):
+    """Returns (status, vsie_solve_info)."""
+    lib = load_library()
+    info = vsie_solve_info()
+    st = lib.vsie_solve(ctx, int(p), C.c_void_p(int(B)), int(ldb), C.c_void_p(int(X)), int(ldx),
+                        float(tol), C.byref(opts) if opts is not None else None, C.byref(info),
+                        C.c_void_p(int(stream)))
+    if check and st not in (VSIE_OK, VSIE_ENOCONV):
+        _check(st, ctx)
+    return st, info
+
+
+def vsie_save(ctx, path):
+    _check(load_library().vsie_save(ctx, str(path).encode()), ctx)
+
+
+def vsie_load(path):
+    out = C.c_void_p()
+    _check(load_library().vsie_load(str(path).encode(), C.byref(out)))
+    return out
+
+
+def vsie_get_parts(ctx):
+    p = vsie_parts()
+    _check(load_library().vsie_get_parts(ctx, C.byref(p)), ctx)
+    return p
+
+
+def vsie_destroy(ctx):
+    if ctx:
+        load_library().vsie_destroy(ctx)
