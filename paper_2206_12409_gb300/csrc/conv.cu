@@ -53,7 +53,7 @@ __device__ __forceinline__ void load_tw(C* s, const C* g, int L) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_xfwd(ConvArgs<R> a, int NL) {
     using C = cx<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* s0 = tw + a.L1;
     C* s1 = s0 + (size_t)NL * a.L1;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_xfwd(ConvArgs<R> a, int NL) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_yfwd(ConvArgs<R> a, int NL) {
     using C = cx<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* s0 = tw + a.L2;
     C* s1 = s0 + (size_t)NL * a.L2;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_yfwd(ConvArgs<R> a, int NL) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_zmul(ConvArgs<R> a, int NL) {
     using C = cx<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf[4];
     buf[0] = tw + a.L3;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_zmul(ConvArgs<R> a, int NL) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_yinv(ConvArgs<R> a, int NL) {
     using C = cx<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* s0 = tw + a.L2;
     C* s1 = s0 + (size_t)NL * a.L2;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(256) k_yinv(ConvArgs<R> a, int NL) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_xinv(ConvArgs<R> a, int NL) {
     using C = cx<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* s0 = tw + a.L1;
     C* s1 = s0 + (size_t)NL * a.L1;

@@ -67,7 +67,7 @@ __global__ void k_generator(double2* __restrict__ t, int L1, int L2, int L3, int
 // axis 0: lines are contiguous; axis 1/2: a CTA takes NL consecutive k1.
 __global__ void k_fft_axis(double2* __restrict__ t, int L1, int L2, int L3, int ncomp, int axis,
                            FFTPlan pl, const double2* __restrict__ twg, int NL) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* tw = reinterpret_cast<double2*>(smem_raw);
     const int L = pl.L;
     double2* s0 = tw + L;
