@@ -51,7 +51,14 @@ bool fft_factor(int L, FFTPlan& pl) {
         while (n % q == 0) { r.push_back(q); n /= q; }
     if (n != 1 || (int)r.size() > kMaxStages) return false;
     pl.nst = (int)r.size();
-    for (int i = 0; i < pl.nst; ++i) pl.rad[i] = r[i];
+    int ns = 1;
+    for (int i = 0; i < pl.nst; ++i) {
+        pl.rad[i] = r[i];
+        pl.ns[i] = ns;
+        pl.nsmagic[i] = magic_div((uint32_t)ns);
+        pl.twstep[i] = L / (ns * r[i]);
+        ns *= r[i];
+    }
     return true;
 }
 

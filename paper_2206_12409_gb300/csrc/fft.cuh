@@ -1,44 +1,25 @@
-// Shared-memory Stockham FFT stages used by the convolution passes (K1) and by
-// the spectra set-up.  A CTA transforms `nl` lines of length L held in shared
-// memory; element (line, k) sits at buf[line * ls + k * ks].  Each stage of
-// radix R reads every element once from `src` and writes it to `dst`
-// (ping-pong), so one barrier per stage suffices.
+// Shared-memory Stockham FFT used by the convolution passes (K1) and by the
+// spectra set-up.  A CTA transforms NLT lines of length L held in shared
+// memory, element (line, k) at buf[k * KS + line] (lines fastest, so that the
+// threads of a warp touch consecutive addresses).  Each stage of radix R reads
+// one buffer and writes the other (ping-pong), so a thread keeps only one
+// butterfly's R values in registers.
 //
-// Stage t (radix R, Ns = product of the radices before it), butterfly j in
-// [0, L/R): k = j mod Ns, inputs src[j + r L/R] twiddled by w^(r k) with
-// w = exp(-+ 2 pi i / (Ns R)), radix-R DFT, outputs to dst[(j - k) R + k + r Ns].
-// Twiddles come from a table tw[m] = exp(-2 pi i m / L) (conjugated for the
-// inverse transform).  The inverse transform is unnormalised.
+// Stage (radix R, Ns = product of the radices before it), butterfly j in
+// [0, L/R): k = j mod Ns, inputs at j + r L/R twiddled by w^(r k) with
+// w = exp(-+ 2 pi i / (Ns R)), radix-R DFT, outputs to (j - k) R + k + r Ns.
+// Twiddles come from tw[m] = exp(-2 pi i m / L) (conjugated for the inverse).
+// The inverse transform is unnormalised.
 #pragma once
 #include "vsie_internal.h"
 
 namespace vsie {
-
-// cos/sin(2 pi k / R) constants
-#define C3S 0.86602540378443864676
-#define C5C1 0.30901699437494742410
-#define C5S1 0.95105651629515357212
-#define C5C2 -0.80901699437494742410
-#define C5S2 0.58778525229247312917
-#define C7C1 0.62348980185873353053
-#define C7S1 0.78183148246802980871
-#define C7C2 -0.22252093395631440429
-#define C7S2 0.97492791218182360702
-#define C7C3 -0.90096886790241912624
-#define C7S3 0.43388373911755812048
-#define SQH 0.70710678118654752440
 
 // multiply by -i (forward) or +i (inverse)
 template <bool INV, typename C> __device__ __forceinline__ C rot90(C a) {
     C r;
     if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
     return r;
-}
-
-template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a0, C& a1) {
-    C t = a0;
-    a0 = cadd(t, a1);
-    a1 = csub(t, a1);
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
@@ -50,8 +31,14 @@ template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a
     a3 = csub(d02, d13);
 }
 
-template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<2>) { dft2<INV>(v[0], v[1]); }
-template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<4>) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<2>) {
+    C t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+}
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<4>) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+}
 
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<8>) {
     using R = decltype(v[0].x);
@@ -61,18 +48,15 @@ template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<
         b[r] = cadd(v[r], v[r + 4]);
         b[r + 4] = csub(v[r], v[r + 4]);
     }
-    // twiddles w8^r, r = 1, 2, 3 on the difference half
-    const R q = (R)SQH;
+    constexpr R q = (R)0.70710678118654752440;
     {
-        C t = b[5];
-        // w8 = (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse
+        C t = b[5];   // times (1 -+ i)/sqrt2
         if (INV) { b[5].x = q * (t.x - t.y); b[5].y = q * (t.x + t.y); }
         else { b[5].x = q * (t.x + t.y); b[5].y = q * (t.y - t.x); }
     }
     b[6] = rot90<INV>(b[6]);
     {
-        C t = b[7];
-        // w8^3 = (-1 - i)/sqrt2 forward, (-1 + i)/sqrt2 inverse
+        C t = b[7];   // times (-1 -+ i)/sqrt2
         if (INV) { b[7].x = -q * (t.x + t.y); b[7].y = q * (t.x - t.y); }
         else { b[7].x = q * (t.y - t.x); b[7].y = -q * (t.x + t.y); }
     }
@@ -84,6 +68,7 @@ template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<
 
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<3>) {
     using R = decltype(v[0].x);
+    constexpr R s3 = (R)0.86602540378443864676;
     C t = cadd(v[1], v[2]);
     C d = csub(v[1], v[2]);
     C a0 = v[0];
@@ -91,18 +76,32 @@ template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<
     C m = a0;
     m.x -= (R)0.5 * t.x;
     m.y -= (R)0.5 * t.y;
-    // (-+ i) s3 d
     C sd = rot90<INV>(d);
-    sd.x *= (R)C3S;
-    sd.y *= (R)C3S;
+    sd.x *= s3;
+    sd.y *= s3;
     v[1] = cadd(m, sd);
     v[2] = csub(m, sd);
 }
 
+// cos / sin (2 pi k / R), k = 1 .. (R-1)/2
+template <typename R, int RR> struct OddConst;
+template <typename R> struct OddConst<R, 5> {
+    __device__ static constexpr R c(int k) { return k == 1 ? (R)0.30901699437494742410 : (R)-0.80901699437494742410; }
+    __device__ static constexpr R s(int k) { return k == 1 ? (R)0.95105651629515357212 : (R)0.58778525229247312917; }
+};
+template <typename R> struct OddConst<R, 7> {
+    __device__ static constexpr R c(int k) {
+        return k == 1 ? (R)0.62348980185873353053 : k == 2 ? (R)-0.22252093395631440429 : (R)-0.90096886790241912624;
+    }
+    __device__ static constexpr R s(int k) {
+        return k == 1 ? (R)0.78183148246802980871 : k == 2 ? (R)0.97492791218182360702 : (R)0.43388373911755812048;
+    }
+};
+
 // odd prime radix by symmetric pairs:
-// A_q = a0 + sum_{r=1}^{(R-1)/2} [ (a_r + a_{R-r}) cos(2 pi r q / R) -+ i (a_r - a_{R-r}) sin(2 pi r q / R) ]
+// A_q = a0 + sum_{r=1}^{H} [ (a_r + a_{R-r}) cos(2 pi r q / R) -+ i (a_r - a_{R-r}) sin(2 pi r q / R) ]
 template <bool INV, int RR, typename C>
-__device__ __forceinline__ void dft_odd(C* v, const double* cs, const double* sn) {
+__device__ __forceinline__ void dft_odd(C* v) {
     using R = decltype(v[0].x);
     constexpr int H = (RR - 1) / 2;
     C sp[H], dm[H];
@@ -115,91 +114,78 @@ __device__ __forceinline__ void dft_odd(C* v, const double* cs, const double* sn
     C s0 = a0;
 #pragma unroll
     for (int r = 0; r < H; ++r) s0 = cadd(s0, sp[r]);
-    C out[RR];
-    out[0] = s0;
+    v[0] = s0;
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
         C re = a0, im = czero<C>();
 #pragma unroll
         for (int r = 1; r <= H; ++r) {
-            const int idx = (r * q) % RR;          // angle index 2 pi idx / R
+            const int idx = (r * q) % RR;
             const int k = idx <= H ? idx : RR - idx;
-            const R c = (R)cs[k - 1];
-            const R s = (R)(idx <= H ? sn[k - 1] : -sn[k - 1]);
+            const R c = OddConst<R, RR>::c(k);
+            const R s = idx <= H ? OddConst<R, RR>::s(k) : -OddConst<R, RR>::s(k);
             re.x += c * sp[r - 1].x;
             re.y += c * sp[r - 1].y;
             im.x += s * dm[r - 1].x;
             im.y += s * dm[r - 1].y;
         }
-        C ri = rot90<INV>(im);   // -i s d forward, +i s d inverse
-        out[q] = cadd(re, ri);
-        out[RR - q] = csub(re, ri);
+        C ri = rot90<INV>(im);
+        // outputs q and R - q; write after all reads of v[1..] are done (sp/dm hold them)
+        v[q] = cadd(re, ri);
+        v[RR - q] = csub(re, ri);
     }
-#pragma unroll
-    for (int q = 0; q < RR; ++q) v[q] = out[q];
 }
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<5>) { dft_odd<INV, 5>(v); }
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<7>) { dft_odd<INV, 7>(v); }
 
-template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<5>) {
-    const double cs[2] = {C5C1, C5C2}, sn[2] = {C5S1, C5S2};
-    dft_odd<INV, 5>(v, cs, sn);
-}
-template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<7>) {
-    const double cs[3] = {C7C1, C7C2, C7C3}, sn[3] = {C7S1, C7S2, C7S3};
-    dft_odd<INV, 7>(v, cs, sn);
-}
-
-template <int RR, bool INV, typename C>
-__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst,
-                                               int nl, int L, int ls, int ks, int Ns,
-                                               const C* __restrict__ tw, bool line_fast) {
+template <int RR, bool INV, int NLT, int KS, typename C>
+__device__ __forceinline__ void stage_pp(const C* __restrict__ src, C* __restrict__ dst, int L,
+                                         int Ns, uint32_t nsmagic, int twstep,
+                                         const C* __restrict__ tw) {
     const int nbf = L / RR;
-    const int total = nl * nbf;
-    const int twstep = L / (Ns * RR);
+    const int total = NLT * nbf;
     for (int it = threadIdx.x; it < total; it += blockDim.x) {
-        int line, j;
-        if (line_fast) { line = it % nl; j = it / nl; }
-        else { line = it / nbf; j = it - line * nbf; }
-        const int k = j % Ns;
-        const C* s = src + (size_t)line * ls;
+        const int line = it % NLT, j = it / NLT;
         C v[RR];
 #pragma unroll
-        for (int r = 0; r < RR; ++r) v[r] = s[(size_t)(j + r * nbf) * ks];
-        if (Ns > 1) {
+        for (int r = 0; r < RR; ++r) v[r] = src[(j + r * nbf) * KS + line];
+        const int k = nsmagic ? j - Ns * (int)__umulhi((uint32_t)j, nsmagic) : 0;
+        if (k) {
+            const int kt = k * twstep;
 #pragma unroll
             for (int r = 1; r < RR; ++r) {
-                const C w = tw[r * k * twstep];
+                const C w = tw[r * kt];
                 v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
             }
         }
         dftR<INV>(v, int_<RR>());
         const int idx = (j - k) * RR + k;
-        C* d = dst + (size_t)line * ls;
 #pragma unroll
-        for (int r = 0; r < RR; ++r) d[(size_t)(idx + r * Ns) * ks] = v[r];
+        for (int r = 0; r < RR; ++r) dst[(idx + r * Ns) * KS + line] = v[r];
     }
 }
 
-// Full transform of nl lines; returns the buffer that holds the result
-// (either `a` or `b`).  Ends with __syncthreads().
-template <bool INV, typename C>
-__device__ C* fft_lines(C* a, C* b, int nl, int L, int ls, int ks, const FFTPlan& pl,
-                        const C* tw, bool line_fast) {
+// Full transform of the NLT lines held in `a` (element (line, k) at
+// a[k * KS + line]); `b` is scratch of the same size.  Returns the buffer that
+// holds the result.  Starts and ends synchronised.
+template <bool INV, int NLT, int KS, typename C>
+__device__ C* fft_pp(C* a, C* b, const FFTPlan& pl, const C* tw) {
     C* src = a;
     C* dst = b;
-    int Ns = 1;
     for (int st = 0; st < pl.nst; ++st) {
-        const int r = pl.rad[st];
-        switch (r) {
-            case 8: stockham_stage<8, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
-            case 4: stockham_stage<4, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
-            case 2: stockham_stage<2, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
-            case 3: stockham_stage<3, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
-            case 5: stockham_stage<5, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
-            default: stockham_stage<7, INV>(src, dst, nl, L, ls, ks, Ns, tw, line_fast); break;
+        const int Ns = pl.ns[st];
+        const uint32_t mg = pl.nsmagic[st];
+        const int ts = pl.twstep[st];
+        switch (pl.rad[st]) {
+            case 8: stage_pp<8, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
+            case 4: stage_pp<4, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
+            case 2: stage_pp<2, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
+            case 3: stage_pp<3, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
+            case 5: stage_pp<5, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
+            default: stage_pp<7, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
         }
         __syncthreads();
         C* t = src; src = dst; dst = t;
-        Ns *= r;
     }
     return src;
 }

@@ -63,36 +63,41 @@ __global__ void k_generator(double2* __restrict__ t, int L1, int L2, int L3, int
     }
 }
 
-// In-place FFT of a full L1 x L2 x L3 x ncomp array along one axis.
-// axis 0: lines are contiguous; axis 1/2: a CTA takes NL consecutive k1.
-__global__ void k_fft_axis(double2* __restrict__ t, int L1, int L2, int L3, int ncomp, int axis,
-                           FFTPlan pl, const double2* __restrict__ twg, int NL) {
+// In-place FFT of a full L1 x L2 x L3 x ncomp array along one axis; a CTA
+// transforms NL lines: consecutive lines along i1 (axis 0: lines are the
+// (k2, k3, comp) rows, loaded transposed) or NL consecutive k1 (axes 1, 2).
+template <int NL>
+__global__ void __launch_bounds__(512) k_fft_axis(double2* __restrict__ t, int L1, int L2, int L3,
+                                                  int ncomp, int axis, FFTPlan pl,
+                                                  const double2* __restrict__ twg) {
+    constexpr int KS = NL + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* tw = reinterpret_cast<double2*>(smem_raw);
     const int L = pl.L;
     double2* s0 = tw + L;
-    double2* s1 = s0 + (size_t)NL * L;
+    double2* s1 = s0 + (size_t)KS * L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
     const size_t vol = (size_t)L1 * L2 * L3;
-    size_t base;
-    size_t es;
-    int nvalid;
     if (axis == 0) {
         const size_t nlines = (size_t)L2 * L3 * ncomp;
         const size_t l0 = (size_t)blockIdx.x * NL;
-        base = l0 * L1;
-        es = 1;
-        nvalid = (int)min((size_t)NL, nlines - l0);
-        for (int e = threadIdx.x; e < NL * L; e += blockDim.x)
-            s0[e] = (e / L) < nvalid ? t[base + e] : make_double2(0, 0);
+        const size_t base = l0 * L1;
+        const int nvalid = (int)min((size_t)NL, nlines - l0);
+        for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
+            const int l = e / L, k = e - l * L;
+            s0[k * KS + l] = l < nvalid ? t[base + e] : make_double2(0, 0);
+        }
         __syncthreads();
-        double2* r = fft_lines<false>(s0, s1, NL, L, L, 1, pl, tw, false);
-        for (int e = threadIdx.x; e < nvalid * L; e += blockDim.x) t[base + e] = r[e];
+        const double2* r = fft_pp<false, NL, KS>(s0, s1, pl, tw);
+        for (int e = threadIdx.x; e < nvalid * L; e += blockDim.x) {
+            const int l = e / L, k = e - l * L;
+            t[base + e] = r[k * KS + l];
+        }
         return;
     }
-    // tiles of NL consecutive k1; blockIdx.y enumerates the other index x comp
     const int k10 = blockIdx.x * NL;
     const int other = blockIdx.y;
+    size_t base, es;
     if (axis == 1) {
         const int k3 = other % L3, c = other / L3;
         base = (size_t)c * vol + (size_t)k3 * L1 * L2;
@@ -104,13 +109,13 @@ __global__ void k_fft_axis(double2* __restrict__ t, int L1, int L2, int L3, int 
     }
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
         const int l = e % NL, k = e / NL;
-        s0[e] = (k10 + l) < L1 ? t[base + k * es + k10 + l] : make_double2(0, 0);
+        s0[k * KS + l] = (k10 + l) < L1 ? t[base + k * es + k10 + l] : make_double2(0, 0);
     }
     __syncthreads();
-    double2* r = fft_lines<false>(s0, s1, NL, L, 1, NL, pl, tw, true);
+    const double2* r = fft_pp<false, NL, KS>(s0, s1, pl, tw);
     for (int e = threadIdx.x; e < NL * L; e += blockDim.x) {
         const int l = e % NL, k = e / NL;
-        if (k10 + l < L1) t[base + k * es + k10 + l] = r[e];
+        if (k10 + l < L1) t[base + k * es + k10 + l] = r[k * KS + l];
     }
 }
 
@@ -165,19 +170,19 @@ void build_spectra(Ctx& c) {
         k_generator<<<2048, 256>>>(t, L1, L2, L3, c.ne[0], c.ne[1], c.ne[2], c.h, c.k0,
                                    make_double2(sv.real(), sv.imag()));
         VSIE_CUDA(cudaGetLastError());
-        const int NL = 8;
-        VSIE_CUDA(cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        constexpr int NL = 8;
+        VSIE_CUDA(cudaFuncSetAttribute(k_fft_axis<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         for (int ax = 0; ax < 3; ++ax) {
             const int L = c.L[ax];
-            const size_t sm = ((size_t)2 * NL + 1) * L * sizeof(double2);
+            const size_t sm = ((size_t)2 * (NL + 1) + 1) * L * sizeof(double2);
             if (ax == 0) {
                 const size_t nlines = (size_t)L2 * L3 * 6;
-                k_fft_axis<<<(unsigned)((nlines + NL - 1) / NL), 256, sm>>>(
-                    t, L1, L2, L3, 6, 0, c.plan[0], c.f64.tw[0], NL);
+                k_fft_axis<NL><<<(unsigned)((nlines + NL - 1) / NL), 256, sm>>>(
+                    t, L1, L2, L3, 6, 0, c.plan[0], c.f64.tw[0]);
             } else {
                 dim3 g((L1 + NL - 1) / NL, (ax == 1 ? L3 : L2) * 6);
-                k_fft_axis<<<g, 256, sm>>>(t, L1, L2, L3, 6, ax, c.plan[ax], c.f64.tw[ax], NL);
+                k_fft_axis<NL><<<g, 256, sm>>>(t, L1, L2, L3, 6, ax, c.plan[ax], c.f64.tw[ax]);
             }
             VSIE_CUDA(cudaGetLastError());
         }

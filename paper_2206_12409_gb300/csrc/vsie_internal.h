@@ -73,7 +73,15 @@ struct FFTPlan {
     int L = 0;
     int nst = 0;
     int rad[kMaxStages] = {0};
+    int ns[kMaxStages] = {0};          // product of the radices before each stage
+    uint32_t nsmagic[kMaxStages] = {0};  // floor(2^32 / ns) + 1 (0 when ns == 1)
+    int twstep[kMaxStages] = {0};      // L / (ns * rad)
 };
+
+// q = x / d for x, d < 2^16 via one multiply-high (exact in that range).
+__host__ __device__ inline uint32_t magic_div(uint32_t d) {
+    return d <= 1 ? 0u : (uint32_t)((0x100000000ull / d) + 1ull);
+}
 
 bool fft_factor(int L, FFTPlan& plan);     // radices 8,4,2,3,5,7; false if L not 7-smooth
 int next_smooth(int n);                    // smallest 7-smooth integer >= n
