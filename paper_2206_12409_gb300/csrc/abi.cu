@@ -12,7 +12,7 @@ namespace vsie {
 static std::mutex g_err_mu;
 static std::string g_err;   // last context-less error
 
-static void set_global_err(const std::string& m) {
+void set_global_err(const std::string& m) {
     std::lock_guard<std::mutex> lk(g_err_mu);
     g_err = m;
 }
@@ -125,7 +125,16 @@ static void prepare_precision(Ctx& c) {
         d.cc = (C*)dalloc(c, sa * sizeof(C));
     }
     if (c.m_f > 0) {
-        d.Zff = up_c<R>(c, c.hZff);
+        if (c.dZff_in) {
+            if (sizeof(R) == 8) {
+                d.Zff = (cx<R>*)c.dZff_in;
+            } else {
+                d.Zff = (cx<R>*)dalloc(c, (size_t)c.m_f * c.m_f * sizeof(cx<R>));
+                convert_to_f32(c.dZff_in, (float2*)d.Zff, (size_t)c.m_f * c.m_f);
+            }
+        } else {
+            d.Zff = up_c<R>(c, c.hZff);
+        }
         if (c.aca_rank > 0 && c.m_n > 0) {
             d.U = up_c<R>(c, c.hU);
             d.V = up_c<R>(c, c.hV);
@@ -160,6 +169,8 @@ static void prepare_precision(Ctx& c) {
     d.splitk_elems = std::max<size_t>((size_t)4 * 1024 * 1024, (size_t)2 * std::max(c.m_f, 1) * p * 8);
     d.splitk = (C*)dalloc(c, d.splitk_elems * sizeof(C));
     conv_set_attrs<R>();
+    VSIE_CUDA(cudaDeviceSynchronize());
+    conv_autotune<R>(c);
     d.ready = true;
 }
 
@@ -344,9 +355,11 @@ static void init_ctx(Ctx& c, const vsie_grid* body, const double* eps_r, const d
     c.line_cidx = upload(c, lci.data(), lci.size());
     c.body_lines = upload(c, flags.data(), flags.size());
     if (c.m_f > 0) {
-        if (!parts->Zff) throw Error(VSIE_EINVAL, "far parts: Zff is required");
-        const auto* Z = reinterpret_cast<const std::complex<double>*>(parts->Zff);
-        c.hZff.assign(Z, Z + (size_t)c.m_f * c.m_f);
+        if (!c.dZff_in) {
+            if (!parts->Zff) throw Error(VSIE_EINVAL, "far parts: Zff is required");
+            const auto* Z = reinterpret_cast<const std::complex<double>*>(parts->Zff);
+            c.hZff.assign(Z, Z + (size_t)c.m_f * c.m_f);
+        }
         c.aca_rank = parts->aca_rank;
         if (c.aca_rank > 0 && c.m_n > 0) {
             if (!parts->U || !parts->V) throw Error(VSIE_EINVAL, "ACA factors missing");
@@ -408,15 +421,56 @@ void destroy_ctx(Ctx* c) {
     delete c;
 }
 
-vsie_status create_from_parts(const vsie_grid* body, const double* eps_r, const double* sigma,
-                              double freq, const vsie_options* opts, const vsie_parts* parts,
-                              vsie_ctx** out) {
+// vsie_get_parts: host views of the operator parts (Zff copied from the device
+// when the set-up produced it there).
+static void fill_parts(Ctx& c, vsie_parts& p) {
+    p = vsie_parts{};
+    p.m_f = c.m_f;
+    p.m_n = c.m_n;
+    p.stencil = c.s;
+    if (c.m_n > 0) {
+        p.W = reinterpret_cast<const double*>(c.hW.data());
+        p.base = c.hBase.data();
+        p.pre_nnz = c.pre_nnz;
+        if (c.pre_nnz > 0) {
+            p.pre_rowptr = c.hPreRow.data();
+            p.pre_col = c.hPreCol.data();
+            p.pre_val = reinterpret_cast<const double*>(c.hPreVal.data());
+        }
+        p.Znn = reinterpret_cast<const double*>(c.hZnn.data());
+    }
+    if (c.m_f > 0) {
+        if (c.hZff.empty()) {
+            c.hZff_copy.resize((size_t)c.m_f * c.m_f);
+            VSIE_CUDA(cudaMemcpy(c.hZff_copy.data(), c.f64.ready ? (const void*)c.f64.Zff : (const void*)c.dZff_in,
+                                 c.hZff_copy.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+            p.Zff = reinterpret_cast<const double*>(c.hZff_copy.data());
+        } else {
+            p.Zff = reinterpret_cast<const double*>(c.hZff.data());
+        }
+        p.aca_rank = c.aca_rank;
+        if (c.aca_rank > 0) {
+            p.U = reinterpret_cast<const double*>(c.hU.data());
+            p.V = reinterpret_cast<const double*>(c.hV.data());
+        }
+        for (int a = 0; a < 3; ++a) {
+            for (int q = 0; q < 3; ++q) p.tt_rank[a][q] = c.tt_rank[a][q];
+            for (int q = 0; q < 4; ++q)
+                p.tt_core[a][q] = c.tt_rank[a][0] ? reinterpret_cast<const double*>(c.hTT[a][q].data()) : nullptr;
+        }
+    }
+}
+
+vsie_status create_from_parts_impl(const vsie_grid* body, const double* eps_r,
+                                   const double* sigma, double freq, const vsie_options* opts,
+                                   const vsie_parts* parts, double2* dZff, Ctx** out) {
     if (!out) { set_global_err("null output pointer"); return VSIE_EINVAL; }
     *out = nullptr;
     Ctx* c = new (std::nothrow) Ctx();
     if (!c) { set_global_err("host allocation failed"); return VSIE_ENOMEM; }
     try {
         VSIE_CUDA(cudaGetDevice(&c->device));
+        c->dZff_in = dZff;
         init_ctx(*c, body, eps_r, sigma, freq, opts, parts);
     } catch (const Error& e) {
         set_global_err(e.msg);
@@ -427,8 +481,18 @@ vsie_status create_from_parts(const vsie_grid* body, const double* eps_r, const 
         destroy_ctx(c);
         return VSIE_ENOMEM;
     }
-    *out = reinterpret_cast<vsie_ctx*>(c);
+    *out = c;
     return VSIE_OK;
+}
+
+vsie_status create_from_parts(const vsie_grid* body, const double* eps_r, const double* sigma,
+                              double freq, const vsie_options* opts, const vsie_parts* parts,
+                              vsie_ctx** out) {
+    if (!out) { set_global_err("null output pointer"); return VSIE_EINVAL; }
+    Ctx* c = nullptr;
+    const vsie_status st = create_from_parts_impl(body, eps_r, sigma, freq, opts, parts, nullptr, &c);
+    *out = reinterpret_cast<vsie_ctx*>(c);
+    return st;
 }
 
 }  // namespace vsie
@@ -486,6 +550,17 @@ vsie_status vsie_matvec(vsie_ctx* ctx, int32_t p, const void* X, int64_t ldx, vo
         } else {
             throw Error(VSIE_EINVAL, "unknown precision");
         }
+    } catch (const Error& e) {
+        return fail(c, e);
+    }
+    return VSIE_OK;
+}
+
+vsie_status vsie_get_parts(vsie_ctx* ctx, vsie_parts* parts) {
+    if (!ctx || !parts) { set_global_err("null context or output"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    try {
+        fill_parts(*c, *parts);
     } catch (const Error& e) {
         return fail(c, e);
     }

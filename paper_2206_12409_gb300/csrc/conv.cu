@@ -57,7 +57,7 @@ __device__ __forceinline__ void load_tw(C* s, const C* g, int L) {
 
 // --------------------------------------------------------------- X forward
 template <typename R, int NL>
-__global__ void __launch_bounds__(512) k_xfwd(ConvArgs<R> a) {
+__global__ void __launch_bounds__(1024) k_xfwd(ConvArgs<R> a) {
     using C = cx<R>;
     constexpr int KS = NL + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -82,16 +82,32 @@ __global__ void __launch_bounds__(512) k_xfwd(ConvArgs<R> a) {
     load_tw(tw, a.tw1, a.L1);
     __syncthreads();
     const C* xb = a.X + (size_t)j * a.ldx + a.xoff + (size_t)comp * a.nb;
-    for (int e = threadIdx.x; e < NL * a.L1; e += blockDim.x) {
-        const int l = udiv(e, a.L1magic), i1 = e - l * a.L1;
-        C v = czero<C>();
-        const int q1 = i1 - a.o1;
-        const int64_t lb = lbase[l];
-        if (lb >= 0 && q1 >= 0 && q1 < a.b1) {
-            const int64_t vb = lb + q1;
-            if (a.mask[vb]) v = xb[vb];
+    constexpr int U = 8;   // independent loads in flight per thread
+    const int tot = NL * a.L1;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = czero<C>();
+            if (e < tot) {
+                const int l = udiv(e, a.L1magic), i1 = e - l * a.L1;
+                const int q1 = i1 - a.o1;
+                const int64_t lb = lbase[l];
+                if (lb >= 0 && q1 >= 0 && q1 < a.b1) {
+                    const int64_t vb = lb + q1;
+                    if (a.mask[vb]) v[u] = xb[vb];
+                }
+            }
         }
-        buf[i1 * KS + l] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) {
+                const int l = udiv(e, a.L1magic), i1 = e - l * a.L1;
+                buf[i1 * KS + l] = v[u];
+            }
+        }
     }
     __syncthreads();
     if (a.nact > 0) {
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(512) k_xfwd(ConvArgs<R> a) {
 
 // --------------------------------------------------------------- Y forward / inverse
 template <typename R, int NL, bool INV>
-__global__ void __launch_bounds__(512) k_ypass(ConvArgs<R> a) {
+__global__ void __launch_bounds__(1024) k_ypass(ConvArgs<R> a) {
     using C = cx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -130,12 +146,23 @@ __global__ void __launch_bounds__(512) k_ypass(ConvArgs<R> a) {
     const int nout = INV ? a.n2 : a.L2;    // rows written
     const C* in = INV ? a.B + ((size_t)ja * a.n3 + i3) * a.L2 * a.L1
                       : a.A + ((size_t)ja * a.n3 + i3) * a.n2 * a.L1;
-    for (int e = threadIdx.x; e < NL * a.L2; e += blockDim.x) {
-        const int l = e % NL, row = e / NL;
-        const int k1 = k10 + l;
-        C v = czero<C>();
-        if (row < nin && k1 < a.L1) v = in[(size_t)row * a.L1 + k1];
-        buf[e] = v;
+    constexpr int U = 8;
+    const int tot = NL * a.L2;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int l = e % NL, row = e / NL;
+            const int k1 = k10 + l;
+            v[u] = czero<C>();
+            if (e < tot && row < nin && k1 < a.L1) v[u] = in[(size_t)row * a.L1 + k1];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) buf[e] = v[u];
+        }
     }
     __syncthreads();
     const C* res = fft_pp<INV, NL, NL>(buf, scr, a.pl2, tw);
@@ -165,13 +192,24 @@ __global__ void __launch_bounds__(1024) k_zmul(ConvArgs<R> a) {
     const size_t plane = (size_t)a.L2 * a.L1;
     const C* in = a.B + (size_t)j * 3 * a.n3 * plane + (size_t)k2 * a.L1;
     const size_t cstride = (size_t)a.n3 * plane;
-    for (int e = threadIdx.x; e < NLT * a.L3; e += blockDim.x) {
-        const int ln = e % NLT, k3 = e / NLT;
-        const int comp = ln / NL, l = ln - comp * NL;
-        const int k1 = k10 + l;
-        C v = czero<C>();
-        if (k3 < a.n3 && k1 < a.L1) v = in[comp * cstride + (size_t)k3 * plane + k1];
-        buf[e] = v;
+    constexpr int U = 8;
+    const int tot = NLT * a.L3;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int ln = e % NLT, k3 = e / NLT;
+            const int comp = ln / NL, l = ln - comp * NL;
+            const int k1 = k10 + l;
+            v[u] = czero<C>();
+            if (e < tot && k3 < a.n3 && k1 < a.L1) v[u] = in[comp * cstride + (size_t)k3 * plane + k1];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) buf[e] = v[u];
+        }
     }
     __syncthreads();
     {
@@ -217,7 +255,7 @@ __global__ void __launch_bounds__(1024) k_zmul(ConvArgs<R> a) {
 
 // --------------------------------------------------------------- X inverse + epilogue
 template <typename R, int NL>
-__global__ void __launch_bounds__(512) k_xinv(ConvArgs<R> a) {
+__global__ void __launch_bounds__(1024) k_xinv(ConvArgs<R> a) {
     using C = cx<R>;
     constexpr int KS = NL + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,9 +288,23 @@ __global__ void __launch_bounds__(512) k_xinv(ConvArgs<R> a) {
     load_tw(tw, a.tw1, a.L1);
     const C* in = a.A + (((size_t)j * 3 + comp) * nlines + lin0) * a.L1;
     const int nvalid = min(NL, nlines - lin0) * a.L1;
-    for (int e = threadIdx.x; e < NL * a.L1; e += blockDim.x) {
-        const int l = udiv(e, a.L1magic), k = e - l * a.L1;
-        buf[k * KS + l] = e < nvalid ? in[e] : czero<C>();
+    constexpr int U = 8;
+    const int tot = NL * a.L1;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < nvalid ? in[e] : czero<C>();
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) {
+                const int l = udiv(e, a.L1magic), k = e - l * a.L1;
+                buf[k * KS + l] = v[u];
+            }
+        }
     }
     __syncthreads();
     const C* res = fft_pp<true, NL, KS>(buf, scr, a.pl1, tw);
@@ -282,15 +334,17 @@ __global__ void __launch_bounds__(512) k_xinv(ConvArgs<R> a) {
 }
 
 // --------------------------------------------------------------- launcher
-template <typename R> struct ConvCfg;
-// lines per CTA (x/y passes, z pass) and threads per CTA, by precision
-template <> struct ConvCfg<float> { static constexpr int NLX = 16, NLZ = 16, TX = 512, TZ = 1024; };
-template <> struct ConvCfg<double> { static constexpr int NLX = 8, NLZ = 8, TX = 512, TZ = 1024; };
+// Each pass has a small set of (lines per CTA, threads per CTA) variants; the
+// autotuner (conv_autotune) times them on the context's own buffers and keeps
+// the fastest per pass.
+struct Variant { int nl, threads; };
+static const Variant kXV[] = {{8, 256}, {16, 256}, {16, 512}, {32, 512}, {32, 1024}};
+static const Variant kZV[] = {{4, 256}, {4, 512}, {8, 512}, {8, 1024}, {16, 1024}};
+constexpr int kNX = sizeof(kXV) / sizeof(kXV[0]);
+constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
 
 template <typename R>
-void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
-                cudaStream_t st) {
-    using CF = ConvCfg<R>;
+static ConvArgs<R> make_args(Ctx& c, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy) {
     OpData<R>& d = data<R>(c);
     ConvArgs<R> a;
     a.n1 = c.ne[0]; a.n2 = c.ne[1]; a.n3 = c.ne[2];
@@ -309,49 +363,136 @@ void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ld
     a.gc = d.gc; a.cc = d.cc; a.A = d.bufA; a.B = d.bufB;
     a.spec = d.spec; a.tw1 = d.tw[0]; a.tw2 = d.tw[1]; a.tw3 = d.tw[2];
     a.pl1 = c.plan[0]; a.pl2 = c.plan[1]; a.pl3 = c.plan[2];
+    return a;
+}
+
+template <typename R, int NL>
+static void launch_x(const ConvArgs<R>& a, int p, int t, bool inv, cudaStream_t st) {
+    const size_t sm = (size_t)a.L1 * (2 * NL + 3) * sizeof(cx<R>);
+    dim3 g((a.n2 * a.n3 + NL - 1) / NL, 3, p);
+    if (inv) k_xinv<R, NL><<<g, t, sm, st>>>(a);
+    else k_xfwd<R, NL><<<g, t, sm, st>>>(a);
+}
+template <typename R, int NL>
+static void launch_y(const ConvArgs<R>& a, int p, int t, bool inv, cudaStream_t st) {
+    const size_t sm = (size_t)a.L2 * (2 * NL + 1) * sizeof(cx<R>);
+    dim3 g((a.L1 + NL - 1) / NL, a.n3, 3 * p);
+    if (inv) k_ypass<R, NL, true><<<g, t, sm, st>>>(a);
+    else k_ypass<R, NL, false><<<g, t, sm, st>>>(a);
+}
+template <typename R, int NL>
+static void launch_z(const ConvArgs<R>& a, int p, int t, cudaStream_t st) {
+    const size_t sm = (size_t)a.L3 * (6 * NL + 1) * sizeof(cx<R>);
+    dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
+    k_zmul<R, NL><<<g, t, sm, st>>>(a);
+}
+
+template <typename R>
+static size_t smem_of(const ConvArgs<R>& a, int pass, int nl) {
     const size_t cs = sizeof(cx<R>);
-    constexpr int NLX = CF::NLX, NLZ = CF::NLZ;
-    const int nlines = a.n2 * a.n3;
-    auto thr = [](int work, int tmax) { int t = ((work + 31) / 32) * 32; return std::max(64, std::min(t, tmax)); };
-    {
-        const size_t sm = (size_t)a.L1 * (2 * NLX + 3) * cs;
-        dim3 g((nlines + NLX - 1) / NLX, 3, p);
-        k_xfwd<R, NLX><<<g, thr(NLX * a.L1 / 4, CF::TX), sm, st>>>(a);
+    if (pass == 0 || pass == 4) return (size_t)a.L1 * (2 * nl + 3) * cs;
+    if (pass == 1 || pass == 3) return (size_t)a.L2 * (2 * nl + 1) * cs;
+    return (size_t)a.L3 * (6 * nl + 1) * cs;
+}
+
+// pass: 0 X-fwd, 1 Y-fwd, 2 Z, 3 Y-inv, 4 X-inv
+template <typename R>
+static void run_pass(const ConvArgs<R>& a, int p, int pass, int var, cudaStream_t st) {
+    if (pass == 2) {
+        const Variant v = kZV[var];
+        switch (v.nl) {
+            case 4: launch_z<R, 4>(a, p, v.threads, st); break;
+            case 8: launch_z<R, 8>(a, p, v.threads, st); break;
+            default: launch_z<R, 16>(a, p, v.threads, st); break;
+        }
+        return;
     }
-    {
-        const size_t sm = (size_t)a.L2 * (2 * NLX + 1) * cs;
-        dim3 g((a.L1 + NLX - 1) / NLX, a.n3, 3 * p);
-        k_ypass<R, NLX, false><<<g, thr(NLX * a.L2 / 4, CF::TX), sm, st>>>(a);
+    const Variant v = kXV[var];
+    const bool inv = pass > 2;
+    if (pass == 0 || pass == 4) {
+        switch (v.nl) {
+            case 8: launch_x<R, 8>(a, p, v.threads, inv, st); break;
+            case 16: launch_x<R, 16>(a, p, v.threads, inv, st); break;
+            default: launch_x<R, 32>(a, p, v.threads, inv, st); break;
+        }
+    } else {
+        switch (v.nl) {
+            case 8: launch_y<R, 8>(a, p, v.threads, inv, st); break;
+            case 16: launch_y<R, 16>(a, p, v.threads, inv, st); break;
+            default: launch_y<R, 32>(a, p, v.threads, inv, st); break;
+        }
     }
-    {
-        const size_t sm = (size_t)a.L3 * (6 * NLZ + 1) * cs;
-        dim3 g((a.L1 + NLZ - 1) / NLZ, a.L2, p);
-        k_zmul<R, NLZ><<<g, thr(3 * NLZ * a.L3 / 4, CF::TZ), sm, st>>>(a);
-    }
-    {
-        const size_t sm = (size_t)a.L2 * (2 * NLX + 1) * cs;
-        dim3 g((a.L1 + NLX - 1) / NLX, a.n3, 3 * p);
-        k_ypass<R, NLX, true><<<g, thr(NLX * a.L2 / 4, CF::TX), sm, st>>>(a);
-    }
-    {
-        const size_t sm = (size_t)a.L1 * (2 * NLX + 3) * cs;
-        dim3 g((nlines + NLX - 1) / NLX, 3, p);
-        k_xinv<R, NLX><<<g, thr(NLX * a.L1 / 4, CF::TX), sm, st>>>(a);
-    }
+}
+
+template <typename R>
+void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                cudaStream_t st) {
+    const ConvArgs<R> a = make_args<R>(c, X, ldx, Y, ldy);
+    const int* tune = data<R>(c).tune;
+    for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, p, pass, tune[pass], st);
     VSIE_CUDA(cudaGetLastError());
+}
+
+// Time every variant of every pass (on the context's buffers; X = Y = a
+// scratch vector) and keep the fastest.  Variants whose shared memory does not
+// fit are skipped.  p = the context's max_rhs.
+template <typename R>
+void conv_autotune(Ctx& c) {
+    OpData<R>& d = data<R>(c);
+    int dev = 0, smax = 0;
+    VSIE_CUDA(cudaGetDevice(&dev));
+    VSIE_CUDA(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int p = std::min(c.max_rhs, 4);
+    cx<R>* xy = (cx<R>*)dalloc(c, (size_t)2 * c.N * p * sizeof(cx<R>));
+    VSIE_CUDA(cudaMemset(xy, 0, (size_t)2 * c.N * p * sizeof(cx<R>)));
+    const ConvArgs<R> a = make_args<R>(c, xy, c.N, xy + (size_t)c.N * p, c.N);
+    cudaEvent_t e0, e1;
+    VSIE_CUDA(cudaEventCreate(&e0));
+    VSIE_CUDA(cudaEventCreate(&e1));
+    for (int pass = 0; pass < 5; ++pass) {
+        const int nv = pass == 2 ? kNZ : kNX;
+        float best = 1e30f;
+        int bi = -1;
+        for (int v = 0; v < nv; ++v) {
+            const int nl = pass == 2 ? kZV[v].nl : kXV[v].nl;
+            if (smem_of(a, pass, nl) > (size_t)smax) continue;
+            run_pass<R>(a, p, pass, v, 0);   // warm-up
+            if (cudaGetLastError() != cudaSuccess) continue;
+            VSIE_CUDA(cudaEventRecord(e0, 0));
+            for (int it = 0; it < 3; ++it) run_pass<R>(a, p, pass, v, 0);
+            VSIE_CUDA(cudaEventRecord(e1, 0));
+            VSIE_CUDA(cudaEventSynchronize(e1));
+            if (cudaGetLastError() != cudaSuccess) continue;
+            float ms = 0;
+            VSIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            d.tune_ms[pass][v] = ms / 3;
+            if (ms < best) { best = ms; bi = v; }
+        }
+        if (bi < 0) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw Error(VSIE_EUNSUPPORTED, "no FFT pass configuration fits this grid");
+        }
+        d.tune[pass] = bi;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 template <typename R>
 void conv_set_attrs() {
-    using CF = ConvCfg<R>;
     const int big = 220 * 1024;
-    VSIE_CUDA(cudaFuncSetAttribute(k_xfwd<R, CF::NLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    VSIE_CUDA(cudaFuncSetAttribute(k_ypass<R, CF::NLX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    VSIE_CUDA(cudaFuncSetAttribute(k_ypass<R, CF::NLX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    VSIE_CUDA(cudaFuncSetAttribute(k_zmul<R, CF::NLZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    VSIE_CUDA(cudaFuncSetAttribute(k_xinv<R, CF::NLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+#define VSIE_ATTR(k) VSIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big))
+    VSIE_ATTR((k_xfwd<R, 8>)); VSIE_ATTR((k_xfwd<R, 16>)); VSIE_ATTR((k_xfwd<R, 32>));
+    VSIE_ATTR((k_xinv<R, 8>)); VSIE_ATTR((k_xinv<R, 16>)); VSIE_ATTR((k_xinv<R, 32>));
+    VSIE_ATTR((k_ypass<R, 8, false>)); VSIE_ATTR((k_ypass<R, 16, false>)); VSIE_ATTR((k_ypass<R, 32, false>));
+    VSIE_ATTR((k_ypass<R, 8, true>)); VSIE_ATTR((k_ypass<R, 16, true>)); VSIE_ATTR((k_ypass<R, 32, true>));
+    VSIE_ATTR((k_zmul<R, 4>)); VSIE_ATTR((k_zmul<R, 8>)); VSIE_ATTR((k_zmul<R, 16>));
+#undef VSIE_ATTR
 }
 
+template void conv_autotune<float>(Ctx&);
+template void conv_autotune<double>(Ctx&);
 template void conv_apply<float>(Ctx&, int, const float2*, int64_t, float2*, int64_t, cudaStream_t);
 template void conv_apply<double>(Ctx&, int, const double2*, int64_t, double2*, int64_t, cudaStream_t);
 template void conv_set_attrs<float>();

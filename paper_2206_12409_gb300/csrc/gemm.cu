@@ -13,7 +13,7 @@ constexpr int BK = 16;
 
 template <typename R, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256)
-k_cgemm(int opA, int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A, int64_t lda,
+k_cgemm(int opA, int opB, int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A, int64_t lda,
         int64_t sA, const cx<R>* __restrict__ B, int64_t ldb, int64_t sB, cx<R> beta,
         cx<R>* __restrict__ C, int64_t ldc, int64_t sC, int batch, int splits,
         const uint8_t* __restrict__ maskB, const uint8_t* __restrict__ maskC,
@@ -58,7 +58,9 @@ k_cgemm(int opA, int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A, 
             const int gk = k0 + k, gn = n0 + n;
             Cx v = czero<Cx>();
             if (gk < K && gn < N) {
-                v = Bb[(size_t)gk + (size_t)gn * ldb];
+                if (opB == OP_N) v = Bb[(size_t)gk + (size_t)gn * ldb];
+                else v = Bb[(size_t)gn + (size_t)gk * ldb];
+                if (opB == OP_H) v.y = -v.y;
                 if (maskB && !maskB[(size_t)gk + (size_t)K * gn]) v = czero<Cx>();
             }
             Bs[k][n] = v;
@@ -126,7 +128,7 @@ __global__ void k_splitk_reduce(int M, int N, int batch, int splits, cx<R> alpha
 }
 
 template <typename R, int BM, int BN, int TM, int TN>
-static void launch(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+static void launch(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
                    int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
                    cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
                    const uint8_t* maskC, cudaStream_t st) {
@@ -146,7 +148,7 @@ static void launch(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const c
         if ((size_t)splits * batch * M * N > d.splitk_elems) splits = 1;
     }
     dim3 g(tm, tn, batch * splits);
-    k_cgemm<R, BM, BN, TM, TN><<<g, 256, 0, st>>>(opA, M, N, K, alpha, A, lda, sA, B, ldb, sB,
+    k_cgemm<R, BM, BN, TM, TN><<<g, 256, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
                                                   beta, C, ldc, sC, batch, splits, maskB, maskC,
                                                   d.splitk);
     if (splits > 1) {
@@ -159,26 +161,43 @@ static void launch(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const c
 }
 
 template <typename R>
-void cgemm(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const cx<R>* A, int64_t lda,
-           int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
-           int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
-           cudaStream_t st) {
+void cgemm2(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+            int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
+            int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
+            cudaStream_t st) {
     if (M <= 0 || N <= 0 || batch <= 0) return;
     if (K <= 0) {
         // C = beta C
         if (beta.x == 1 && beta.y == 0) return;
     }
     if (N <= 8)
-        launch<R, 128, 8, 4, 1>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+        launch<R, 128, 8, 4, 1>(c, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
                                 batch, maskB, maskC, st);
     else if (N <= 16)
-        launch<R, 64, 16, 2, 2>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+        launch<R, 64, 16, 2, 2>(c, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
                                 batch, maskB, maskC, st);
     else
-        launch<R, 64, 64, 4, 4>(c, opA, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+        launch<R, 64, 64, 4, 4>(c, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
                                 batch, maskB, maskC, st);
 }
 
+template <typename R>
+void cgemm(Ctx& c, GemmOp opA, int M, int N, int K, cx<R> alpha, const cx<R>* A, int64_t lda,
+           int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
+           int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
+           cudaStream_t st) {
+    cgemm2<R>(c, opA, OP_N, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+              maskB, maskC, st);
+}
+
+template void cgemm2<double>(Ctx&, GemmOp, GemmOp, int, int, int, double2, const double2*,
+                             int64_t, int64_t, const double2*, int64_t, int64_t, double2,
+                             double2*, int64_t, int64_t, int, const uint8_t*, const uint8_t*,
+                             cudaStream_t);
+template void cgemm2<float>(Ctx&, GemmOp, GemmOp, int, int, int, float2, const float2*,
+                            int64_t, int64_t, const float2*, int64_t, int64_t, float2,
+                            float2*, int64_t, int64_t, int, const uint8_t*, const uint8_t*,
+                            cudaStream_t);
 template void cgemm<float>(Ctx&, GemmOp, int, int, int, float2, const float2*, int64_t, int64_t,
                            const float2*, int64_t, int64_t, float2, float2*, int64_t, int64_t,
                            int, const uint8_t*, const uint8_t*, cudaStream_t);

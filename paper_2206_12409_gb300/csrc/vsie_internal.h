@@ -119,6 +119,8 @@ struct OpData {
     cx<R>* t4 = nullptr;
     cx<R>* splitk = nullptr;    // split-K partial sums
     size_t splitk_elems = 0;
+    int tune[5] = {0, 0, 0, 0, 0};     // chosen FFT pass variants (autotuned)
+    float tune_ms[5][8] = {{0}};       // measured time per variant (ms, p = min(max_rhs, 4))
     bool ready = false;
 };
 
@@ -179,6 +181,9 @@ struct Ctx {
     double2* kr_Z = nullptr;           // flexible directions (FP32 stored as float2)
     size_t kr_bytes = 0;
     bool owns_all = true;
+    double2* dZff_in = nullptr;        // far-far block handed over on the device (FP64)
+    vsie_parts parts_view{};           // filled by vsie_get_parts
+    std::vector<std::complex<double>> hZff_copy;
 };
 
 template <typename R> OpData<R>& data(Ctx& c);
@@ -202,6 +207,8 @@ struct Error {
 };
 
 void* dalloc(Ctx& c, size_t bytes);  // cudaMalloc tracked in c.allocs, throws ENOMEM
+void set_global_err(const std::string& m);  // message for vsie_last_error(NULL)
+void convert_to_f32(const double2* a, float2* b, size_t n);
 
 // launchers (defined in conv.cu / surface.cu)
 template <typename R>
@@ -215,6 +222,8 @@ void surface_pre(Ctx& c, int p, const cx<R>* X, int64_t ldx, cudaStream_t st);
 template <typename R>
 void conv_set_attrs();
 template <typename R>
+void conv_autotune(Ctx& c);
+template <typename R>
 void upload_twiddles(Ctx& c);
 
 enum GemmOp { OP_N = 0, OP_T = 1, OP_H = 2, OP_R = 3 };  // R = conj, no transpose
@@ -227,6 +236,12 @@ void cgemm(Ctx& c, GemmOp opA, int M, int Nn, int K, cx<R> alpha, const cx<R>* A
            int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
            int64_t ldc, int64_t sC, int batch, const uint8_t* maskB, const uint8_t* maskC,
            cudaStream_t st);
+
+template <typename R>
+void cgemm2(Ctx& c, GemmOp opA, GemmOp opB, int M, int Nn, int K, cx<R> alpha, const cx<R>* A,
+            int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
+            cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
+            const uint8_t* maskC, cudaStream_t st);
 
 // volume spectra set-up (green.cu)
 template <typename R>

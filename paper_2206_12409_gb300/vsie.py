@@ -285,3 +285,68 @@ def vsie_get_parts(ctx):
 def vsie_destroy(ctx):
     if ctx:
         load_library().vsie_destroy(ctx)
+
+
+def parts_to_numpy(ctx, body_n):
+    """Copy the context's operator parts into numpy arrays (dict)."""
+    p = vsie_get_parts(ctx)
+
+    def carr(ptr, n):
+        if not ptr or n == 0:
+            return np.zeros(0, np.complex128)
+        buf = (C.c_double * (2 * n)).from_address(ptr)
+        return np.frombuffer(buf, np.float64).copy().view(np.complex128)
+
+    def iarr(ptr, n, ct=C.c_int32, dt=np.int32):
+        if not ptr or n == 0:
+            return np.zeros(0, dt)
+        return np.frombuffer((ct * n).from_address(ptr), dt).copy()
+
+    n1, n2, n3 = body_n
+    nb = n1 * n2 * n3
+    out = {"m_f": p.m_f, "m_n": p.m_n, "stencil": p.stencil}
+    s3 = p.stencil ** 3
+    if p.m_n:
+        out["W"] = carr(p.W, p.m_n * 3 * s3).reshape(p.m_n, 3 * s3)
+        out["base"] = iarr(p.base, p.m_n * 3).reshape(p.m_n, 3)
+        out["Znn"] = carr(p.Znn, p.m_n * p.m_n).reshape(p.m_n, p.m_n, order="F")
+        out["pre_nnz"] = p.pre_nnz
+        if p.pre_nnz:
+            out["pre_rowptr"] = iarr(p.pre_rowptr, 3 * nb + 1, C.c_int64, np.int64)
+            out["pre_col"] = iarr(p.pre_col, p.pre_nnz)
+            out["pre_val"] = carr(p.pre_val, p.pre_nnz)
+    if p.m_f:
+        out["Zff"] = carr(p.Zff, p.m_f * p.m_f).reshape(p.m_f, p.m_f, order="F")
+        k = p.aca_rank
+        out["U"] = carr(p.U, p.m_n * k).reshape(p.m_n, k, order="F")
+        out["V"] = carr(p.V, p.m_f * k).reshape(p.m_f, k, order="F")
+        tt = []
+        for a in range(3):
+            r1, r2, r3 = p.tt_rank[a][0], p.tt_rank[a][1], p.tt_rank[a][2]
+            if r1 == 0:
+                tt.append(None)
+                continue
+            tt.append([carr(p.tt_core[a][0], n1 * r1).reshape(n1, r1, order="F"),
+                       carr(p.tt_core[a][1], r1 * n2 * r2).reshape(r1, n2, r2, order="F"),
+                       carr(p.tt_core[a][2], r2 * n3 * r3).reshape(r2, n3, r3, order="F"),
+                       carr(p.tt_core[a][3], r3 * p.m_f).reshape(r3, p.m_f, order="F")])
+        out["tt"] = tt
+    return out
+
+
+def setup_problem(prob, max_rhs=8, precisions=0):
+    """vsie_setup for an inputs.Problem (geometry marshalling only)."""
+    g = prob.grid
+    coil = shield = None
+    keep = []
+    if prob.coil is not None:
+        coil, k1 = make_mesh(prob.coil.xyz, prob.coil.tri, prob.coil.ports)
+        keep.append(k1)
+    if prob.shield is not None:
+        shield, k2 = make_mesh(prob.shield.xyz, prob.shield.tri, prob.shield.ports)
+        keep.append(k2)
+    opts = make_options(ext_n=prob.ext_n, ext_offset=prob.ext_offset, stencil=prob.stencil,
+                        tt_tol=prob.tt_tol, aca_tol=prob.aca_tol, max_rhs=max_rhs,
+                        precisions=precisions)
+    return vsie_setup(make_grid(g.n, g.h, g.origin), prob.eps_r, prob.sigma, coil, shield,
+                      prob.freq_hz, opts)

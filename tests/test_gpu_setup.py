@@ -1,0 +1,89 @@
+"""GPU set-up from geometry (vsie_setup) against the oracle's definitions, on
+the sphere + loop + closed-shield workload: deterministic parts to ~1e-9,
+compressed parts to their tolerances, and the whole operator against the
+oracle's hybrid and dense operators."""
+import numpy as np
+import pytest
+
+from paper_2206_12409_gb300 import inputs as I
+from oracle import hybrid, coupling, rwg, tt as ott, physics
+from tests.conftest import gpu_matvec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup_ctx(sphere_loop_shield):
+    from paper_2206_12409_gb300 import vsie as V
+    ctx = V.setup_problem(sphere_loop_shield, max_rhs=8)
+    parts = V.parts_to_numpy(ctx, sphere_loop_shield.grid.n)
+    yield ctx, parts
+    V.vsie_destroy(ctx)
+
+
+def test_sizes(setup_ctx, hybrid_parts):
+    from paper_2206_12409_gb300 import vsie as V
+    ctx, parts = setup_ctx
+    assert V.vsie_sizes(ctx) == (hybrid_parts.N, hybrid_parts.m_f, hybrid_parts.m_n,
+                                 hybrid_parts.body.nv)
+
+
+def test_projection_and_stencils(setup_ctx, hybrid_parts):
+    _, parts = setup_ctx
+    P = hybrid_parts
+    assert np.array_equal(parts["base"], P.base)
+    assert np.linalg.norm(parts["W"] - P.W) <= 1e-8 * np.linalg.norm(P.W)
+
+
+def test_precorrection(setup_ctx, hybrid_parts):
+    _, parts = setup_ctx
+    pre = hybrid_parts.pre.tocsr()
+    pre.sort_indices()
+    assert np.array_equal(parts["pre_rowptr"], pre.indptr)
+    assert np.array_equal(parts["pre_col"], pre.indices)
+    assert np.linalg.norm(parts["pre_val"] - pre.data) <= 1e-8 * np.linalg.norm(pre.data)
+
+
+def test_near_block(setup_ctx, hybrid_parts):
+    _, parts = setup_ctx
+    Z = hybrid_parts.Znn
+    assert np.linalg.norm(parts["Znn"] - Z) <= 1e-9 * np.linalg.norm(Z)
+
+
+def test_far_blocks(setup_ctx, hybrid_parts, dense_reference):
+    _, parts = setup_ctx
+    P = hybrid_parts
+    assert np.linalg.norm(parts["Zff"] - P.Zff) <= 1e-10 * np.linalg.norm(P.Zff)
+    Zfn = P.U @ P.V.conj().T     # oracle ACA is exact (full rank) at this size
+    Zg = parts["U"] @ parts["V"].conj().T
+    assert np.linalg.norm(Zg - Zfn) <= 1e-5 * np.linalg.norm(Zfn)
+
+
+def test_tt_against_exact_far_coupling(setup_ctx, sphere_loop_shield):
+    """TT reconstruction vs the exact (1 x 1-point) far coupling on every entry,
+    within the TT tolerance."""
+    _, parts = setup_ctx
+    prob = sphere_loop_shield
+    _, k0 = physics.omega_k0(prob.freq_hz)
+    rs = rwg.build(prob.shield)
+    K = coupling.K_block(prob.grid, np.arange(prob.grid.nv), rs, np.arange(rs.m), k0, near=False)
+    for a in range(3):
+        T = -K[a].reshape(tuple(prob.grid.n) + (rs.m,), order="F")
+        R = ott.tt_full(parts["tt"][a])
+        assert np.linalg.norm(R - T) <= prob.tt_tol * np.linalg.norm(T)
+
+
+def test_matvec_vs_oracle_hybrid_and_dense(setup_ctx, sphere_loop_shield, hybrid_parts,
+                                           dense_reference):
+    from paper_2206_12409_gb300 import vsie as V
+    ctx, _ = setup_ctx
+    P = hybrid_parts
+    x = I.random_vectors(P.N, 2, seed=5)
+    M3 = np.tile(P.chi != 0, 3)
+    x[P.m_f + P.m_n:][~M3] = 0
+    y = gpu_matvec(ctx, x, V.VSIE_C128)
+    yh = hybrid.matvec(P, x)
+    assert np.linalg.norm(y - yh) <= 2e-6 * np.linalg.norm(yh)
+    Z, idx = dense_reference
+    yd = hybrid.dense_matvec(sphere_loop_shield, Z, idx, x)
+    assert np.linalg.norm(y - yd) <= 2e-3 * np.linalg.norm(yd)
