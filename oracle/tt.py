@@ -41,8 +41,11 @@ def tt_svd(A, tol):
 
 
 def tt_full(cores):
+    """Dense tensor of Eq. (TT), contracted one core at a time."""
     G1, G2, G3, G4 = cores
-    return np.einsum("ia,ajb,bkc,cl->ijkl", G1, G2, G3, G4)
+    T = np.tensordot(G1, G2, axes=(1, 0))        # (n1, n2, r2)
+    T = np.tensordot(T, G3, axes=(2, 0))         # (n1, n2, n3, r3)
+    return np.tensordot(T, G4, axes=(3, 0))      # (n1, n2, n3, n4)
 
 
 def tt_matvec(cores, x):
