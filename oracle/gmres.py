@@ -22,6 +22,7 @@ def gmres(A, b, tol=1e-6, restart=50, maxit=10000, M=None, x0=None):
     if bn == 0:
         return np.zeros(n, np.complex128), {"iters": 0, "relres": 0.0, "hist": hist}
     it = 0
+    est_last = 1.0
     r = b - A(x) if np.any(x) else b.copy()
     beta = np.linalg.norm(r)
     hist.append(beta / bn)
@@ -46,9 +47,10 @@ def gmres(A, b, tol=1e-6, restart=50, maxit=10000, M=None, x0=None):
             H[j + 1, j] = np.linalg.norm(w)
             if H[j + 1, j] != 0:
                 V[j + 1] = w / H[j + 1, j]
+            # previous rotations G_i = [[conj(c), conj(s)], [-s, c]] (unitary)
             for i in range(j):
-                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
-                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + np.conj(cs[i]) * H[i + 1, j]
+                t = np.conj(cs[i]) * H[i, j] + np.conj(sn[i]) * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
                 H[i, j] = t
             den = np.sqrt(abs(H[j, j]) ** 2 + abs(H[j + 1, j]) ** 2)
             if den == 0:
@@ -65,10 +67,12 @@ def gmres(A, b, tol=1e-6, restart=50, maxit=10000, M=None, x0=None):
             hist.append(abs(g[j + 1]) / bn)
             if abs(g[j + 1]) / bn <= tol or it >= maxit:
                 break
+        est_last = abs(g[k]) / bn
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
         basis = Zs[:k] if M is not None else V[:k]
         x = x + basis.T @ y
         r = b - A(x)
         beta = np.linalg.norm(r)
         hist[-1] = beta / bn
-    return x, {"iters": it, "relres": beta / bn, "hist": hist}
+    return x, {"iters": it, "relres": beta / bn, "hist": hist,
+               "est": est_last if it else beta / bn}

@@ -1,0 +1,519 @@
+// K7 and the solver: restarted GMRES for p right-hand sides at once (Sec. III.A:
+// GMRES with restart; Saad and Schultz 1986), each RHS with its own Krylov space
+// and one shared multi-RHS matvec per iteration.
+//
+//  mode 0 (plain FP64): GMRES(m), FP64 matvec, classical Gram-Schmidt with one
+//         re-orthogonalisation pass (CGS2), Givens rotations, true residual
+//         recomputed at every restart.
+//  mode 1 (mixed): iterative refinement.  The outer loop forms the FP64
+//         residual r = b - Z x with the FP64 matvec; the inner solve is a
+//         flexible GMRES whose matvec is the FP32 operator (the FP64 basis
+//         vector is rounded to FP32, multiplied, and widened back); the
+//         orthogonalisation (CGS) and the Givens updates stay in FP64.
+// The Krylov basis is stored [i][c][n] (basis index, RHS, row), N rows each.
+// Dot products use a fixed two-stage reduction (deterministic results).
+#include "vsie_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+
+namespace vsie {
+
+template <typename R>
+void matvec_internal(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                     cudaStream_t st);
+
+constexpr int kDotGroup = 8;     // basis vectors per dot-product group
+constexpr int kDotBlocks = 64;   // row chunks per (column, group)
+
+// partial[(blk * ncol + c) * nvec + i] = sum_{n in chunk} conj(V_i[c][n]) w[c][n]
+__global__ void __launch_bounds__(256)
+k_block_dot(const double2* __restrict__ V, int nvec, int64_t N, int p, const double2* __restrict__ w,
+            int64_t ldw, double2* __restrict__ partial) {
+    const int c = blockIdx.y;
+    const int g0 = blockIdx.z * kDotGroup;
+    const int ng = min(kDotGroup, nvec - g0);
+    const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    double2 acc[kDotGroup];
+#pragma unroll
+    for (int g = 0; g < kDotGroup; ++g) acc[g] = make_double2(0, 0);
+    const double2* wc = w + (size_t)c * ldw;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+        const double2 x = wc[n];
+#pragma unroll
+        for (int g = 0; g < kDotGroup; ++g) {
+            if (g < ng) {
+                const double2 v = V[((size_t)(g0 + g) * p + c) * N + n];
+                // conj(v) * x
+                acc[g].x += v.x * x.x + v.y * x.y;
+                acc[g].y += v.x * x.y - v.y * x.x;
+            }
+        }
+    }
+    __shared__ double2 red[kDotGroup][256];
+#pragma unroll
+    for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = acc[g];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = cadd(red[g][threadIdx.x], red[g][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x < ng)
+        partial[((size_t)blockIdx.x * p + c) * nvec + g0 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int p, int nvec,
+                              double2* __restrict__ h) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p * nvec) return;
+    double2 s = make_double2(0, 0);
+    for (int b = 0; b < nblk; ++b) s = cadd(s, partial[(size_t)b * p * nvec + e]);
+    h[e] = s;   // h[c * nvec + i]
+}
+
+// w[c][n] += sgn * sum_i V_i[c][n] * h[c * nvec + i]
+__global__ void k_basis_update(const double2* __restrict__ V, int nvec, int64_t N, int p,
+                               const double2* __restrict__ h, double sgn, double2* __restrict__ w,
+                               int64_t ldw) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        double2 s = make_double2(0, 0);
+        for (int i = 0; i < nvec; ++i) cfma(s, V[((size_t)i * p + c) * N + n], h[c * nvec + i]);
+        double2& t = w[(size_t)c * ldw + n];
+        t.x += sgn * s.x;
+        t.y += sgn * s.y;
+    }
+}
+
+// dst[c][n] = src[c][n] * scale[c]  (scale complex)
+__global__ void k_scale_cols(const double2* __restrict__ src, int64_t lds, int64_t N, int p,
+                             const double2* __restrict__ scale, double2* __restrict__ dst, int64_t ldd) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        dst[(size_t)c * ldd + n] = cmul(src[(size_t)c * lds + n], scale[c]);
+    }
+}
+
+__global__ void k_sub(const double2* __restrict__ a, int64_t lda, const double2* __restrict__ b,
+                      int64_t ldb, int64_t N, int p, double2* __restrict__ out, int64_t ldo) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        out[(size_t)c * ldo + n] = csub(a[(size_t)c * lda + n], b[(size_t)c * ldb + n]);
+    }
+}
+
+__global__ void k_narrow(const double2* __restrict__ a, int64_t N, int p, float2* __restrict__ b) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+__global__ void k_widen(const float2* __restrict__ a, int64_t N, int p, double2* __restrict__ b) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = make_double2(a[e].x, a[e].y);
+}
+
+static int nblk(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+struct Krylov {
+    Ctx& c;
+    int p;
+    int64_t N;
+    int m;
+    double2* V;        // (m+1) x p x N
+    double2* w;        // p x N
+    double2* h;        // p x (m+1)
+    double2* part;     // kDotBlocks x p x (m+1)
+    double2* scl;      // p
+    float2* x32;       // p x N
+    float2* y32;       // p x N
+    cudaStream_t st;
+
+    // h[c][i] = V_i^H w for i < nvec (device h), copied to host hh
+    void dots(int nvec, std::vector<std::complex<double>>& hh) {
+        dim3 g(kDotBlocks, p, (nvec + kDotGroup - 1) / kDotGroup);
+        k_block_dot<<<g, 256, 0, st>>>(V, nvec, N, p, w, N, part);
+        k_reduce_dots<<<(p * nvec + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, nvec, h);
+        VSIE_CUDA(cudaGetLastError());
+        hh.resize((size_t)p * nvec);
+        VSIE_CUDA(cudaMemcpyAsync(hh.data(), h, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        VSIE_CUDA(cudaStreamSynchronize(st));
+    }
+    // squared norms of the columns of w
+    void norms(std::vector<double>& nn) {
+        // w against itself: treat w as a one-vector basis
+        dim3 g(kDotBlocks, p, 1);
+        k_block_dot<<<g, 256, 0, st>>>(w, 1, N, p, w, N, part);
+        k_reduce_dots<<<(p + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, 1, h);
+        VSIE_CUDA(cudaGetLastError());
+        std::vector<double2> t(p);
+        VSIE_CUDA(cudaMemcpyAsync(t.data(), h, p * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        VSIE_CUDA(cudaStreamSynchronize(st));
+        nn.resize(p);
+        for (int c2 = 0; c2 < p; ++c2) nn[c2] = t[c2].x;
+    }
+    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, double2* tgt,
+                int64_t ld) {
+        VSIE_CUDA(cudaMemcpyAsync(h, hh.data(), (size_t)p * nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
+        k_basis_update<<<nblk(N * p), 256, 0, st>>>(V, nvec, N, p, h, sgn, tgt, ld);
+        VSIE_CUDA(cudaGetLastError());
+    }
+    void scale_into(const double2* src, int64_t lds, const std::vector<std::complex<double>>& s,
+                    double2* dst, int64_t ldd) {
+        VSIE_CUDA(cudaMemcpyAsync(scl, s.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
+        k_scale_cols<<<nblk(N * p), 256, 0, st>>>(src, lds, N, p, scl, dst, ldd);
+        VSIE_CUDA(cudaGetLastError());
+    }
+    double2* basis(int i) { return V + (size_t)i * p * N; }
+};
+
+using cdd = std::complex<double>;
+
+// One restarted GMRES(m) solve of A e = r (A applied through `apply`, FP64 in
+// and out) for all p columns, relative tolerance tol with respect to
+// ||r||; returns the correction in e (p x N, ld N).  iters[c] accumulates the
+// iterations until column c met its tolerance.
+template <typename Apply>
+static void gmres_core(Krylov& K, const double2* r, double tol, int maxit, bool cgs2, Apply apply,
+                       double2* e, std::vector<int>& iters, std::vector<double>& relres_est,
+                       int& nmatvec) {
+    const int p = K.p;
+    const int64_t N = K.N;
+    const int m = K.m;
+    VSIE_CUDA(cudaMemsetAsync(e, 0, (size_t)N * p * sizeof(double2), K.st));
+    // residual of the current correction: starts as r
+    double2* res = K.w;
+    VSIE_CUDA(cudaMemcpyAsync(res, r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, K.st));
+    std::vector<double> nr0;
+    K.norms(nr0);
+    std::vector<double> beta0(p);
+    for (int c = 0; c < p; ++c) beta0[c] = std::sqrt(nr0[c]);
+    std::vector<bool> done(p, false);
+    for (int c = 0; c < p; ++c)
+        if (!(beta0[c] > 0)) done[c] = true;
+    relres_est.assign(p, 0.0);
+    int total = 0;
+    while (total < maxit) {
+        // residual norms of this cycle
+        std::vector<double> nr;
+        K.norms(nr);
+        std::vector<double> beta(p);
+        bool all = true;
+        for (int c = 0; c < p; ++c) {
+            beta[c] = std::sqrt(nr[c]);
+            if (!std::isfinite(beta[c])) throw Error(VSIE_EBREAKDOWN, "non-finite residual");
+            if (beta0[c] > 0 && beta[c] <= tol * beta0[c]) done[c] = true;
+            relres_est[c] = beta0[c] > 0 ? beta[c] / beta0[c] : 0.0;
+            all = all && done[c];
+        }
+        if (all) break;
+        // v0 = res / beta
+        std::vector<cdd> sc(p);
+        for (int c = 0; c < p; ++c) sc[c] = beta[c] > 0 ? 1.0 / beta[c] : 0.0;
+        K.scale_into(res, N, sc, K.basis(0), N);
+        std::vector<std::vector<cdd>> H(p, std::vector<cdd>((size_t)(m + 1) * m, 0.0));
+        std::vector<std::vector<cdd>> cs(p, std::vector<cdd>(m)), sn(p, std::vector<cdd>(m));
+        std::vector<std::vector<cdd>> g(p, std::vector<cdd>(m + 1, 0.0));
+        for (int c = 0; c < p; ++c) g[c][0] = beta[c];
+        std::vector<bool> cyc_done(done);
+        int j = 0;
+        for (; j < m && total < maxit; ++j) {
+            apply(K.basis(j), K.w);   // w = A v_j
+            ++nmatvec;
+            std::vector<cdd> hh, hh2;
+            K.dots(j + 1, hh);
+            K.update(j + 1, hh, -1.0, K.w, N);
+            if (cgs2) {
+                K.dots(j + 1, hh2);
+                K.update(j + 1, hh2, -1.0, K.w, N);
+                for (size_t q = 0; q < hh.size(); ++q) hh[q] += hh2[q];
+            }
+            std::vector<double> nw;
+            K.norms(nw);
+            std::vector<cdd> inv(p);
+            ++total;
+            for (int c = 0; c < p; ++c) {
+                const double hn = std::sqrt(nw[c]);
+                if (!std::isfinite(hn)) throw Error(VSIE_EBREAKDOWN, "non-finite Arnoldi vector");
+                std::vector<cdd>& Hc = H[c];
+                for (int i = 0; i <= j; ++i) Hc[i + (size_t)(m + 1) * j] = hh[(size_t)c * (j + 1) + i];
+                Hc[j + 1 + (size_t)(m + 1) * j] = hn;
+                inv[c] = hn > 1e-300 * std::max(beta0[c], 1e-300) ? 1.0 / hn : 0.0;
+                // apply previous rotations to the new column
+                // rotations G_i = [[conj(c), conj(s)], [-s, c]] (unitary), the same
+                // form as the new rotation below
+                for (int i = 0; i < j; ++i) {
+                    const cdd a = Hc[i + (size_t)(m + 1) * j], b = Hc[i + 1 + (size_t)(m + 1) * j];
+                    Hc[i + (size_t)(m + 1) * j] = std::conj(cs[c][i]) * a + std::conj(sn[c][i]) * b;
+                    Hc[i + 1 + (size_t)(m + 1) * j] = -sn[c][i] * a + cs[c][i] * b;
+                }
+                const cdd a = Hc[j + (size_t)(m + 1) * j], b = Hc[j + 1 + (size_t)(m + 1) * j];
+                const double den = std::sqrt(std::norm(a) + std::norm(b));
+                if (den == 0.0) { cs[c][j] = 1.0; sn[c][j] = 0.0; }
+                else { cs[c][j] = a / den; sn[c][j] = b / den; }
+                Hc[j + (size_t)(m + 1) * j] = std::conj(cs[c][j]) * a + std::conj(sn[c][j]) * b;
+                Hc[j + 1 + (size_t)(m + 1) * j] = 0.0;
+                g[c][j + 1] = -sn[c][j] * g[c][j];
+                g[c][j] = std::conj(cs[c][j]) * g[c][j];
+                const double est = std::abs(g[c][j + 1]) / (beta0[c] > 0 ? beta0[c] : 1.0);
+                if (!cyc_done[c]) {
+                    iters[c]++;
+                    relres_est[c] = est;
+                    if (est <= tol || inv[c] == 0.0) cyc_done[c] = true;
+                }
+            }
+            bool all2 = true;
+            for (int c = 0; c < p; ++c) all2 = all2 && cyc_done[c];
+            if (j + 1 < m) K.scale_into(K.w, N, inv, K.basis(j + 1), N);
+            if (all2) { ++j; break; }
+        }
+        // y = H^-1 g (upper triangular, k = j columns); e += V y
+        const int k = j;
+        std::vector<cdd> Y((size_t)p * k, 0.0);
+        for (int c = 0; c < p; ++c) {
+            if (done[c]) continue;
+            for (int i = k - 1; i >= 0; --i) {
+                cdd s = g[c][i];
+                for (int q = i + 1; q < k; ++q) s -= H[c][i + (size_t)(m + 1) * q] * Y[(size_t)c * k + q];
+                const cdd d = H[c][i + (size_t)(m + 1) * i];
+                Y[(size_t)c * k + i] = d != 0.0 ? s / d : 0.0;
+            }
+        }
+        K.update(k, Y, 1.0, e, N);
+        // true residual of the correction: res = r - A e
+        apply(e, K.w);
+        ++nmatvec;
+        k_sub<<<nblk(N * p), 256, 0, K.st>>>(r, N, K.w, N, N, p, K.w, N);
+        VSIE_CUDA(cudaGetLastError());
+        for (int c = 0; c < p; ++c) done[c] = done[c] || cyc_done[c];
+        // (loop re-evaluates the true residual norms at the top)
+    }
+    std::vector<double> nr;
+    K.norms(nr);
+    for (int c = 0; c < p; ++c) relres_est[c] = beta0[c] > 0 ? std::sqrt(nr[c]) / beta0[c] : 0.0;
+}
+
+struct SolveWork {
+    double2 *V = nullptr, *w = nullptr, *h = nullptr, *part = nullptr, *scl = nullptr;
+    double2 *r = nullptr, *e = nullptr, *Ax = nullptr;
+    float2 *x32 = nullptr, *y32 = nullptr;
+};
+
+vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X, int64_t ldx,
+                       double tol, const vsie_solve_opts* o_in, vsie_solve_info* info,
+                       cudaStream_t st) {
+    vsie_solve_opts o{};
+    if (o_in) o = *o_in;
+    const int m = o.restart > 0 ? o.restart : 50;
+    const int maxit = o.maxit > 0 ? o.maxit : 2000;
+    const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+    const int max_outer = o.max_outer > 0 ? o.max_outer : 20;
+    if (!(tol > 0)) throw Error(VSIE_EINVAL, "tol must be > 0");
+    if (p < 1 || p > c.max_rhs) throw Error(VSIE_EINVAL, "p outside [1, max_rhs]");
+    if (ldb < c.N || ldx < c.N) throw Error(VSIE_EINVAL, "leading dimension < N");
+    if (!c.f64.ready) throw Error(VSIE_EUNSUPPORTED, "vsie_solve needs the C128 operator");
+    if (o.mode == 1 && !c.f32.ready) throw Error(VSIE_EUNSUPPORTED, "mode 1 needs the C64 operator");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t N = c.N;
+    // workspace (kept in the context between solves)
+    const size_t need = ((size_t)(m + 1) * p * N + 4 * (size_t)p * N) * sizeof(double2) +
+                        2 * (size_t)p * N * sizeof(float2) +
+                        ((size_t)kDotBlocks * p * (m + 1) + (size_t)p * (m + 1) + p) * sizeof(double2) +
+                        16 * 256;   // slack for the 256-byte alignment of each slice below
+    if (c.kr_bytes < need) {
+        if (c.kr_V) {
+            auto& al = c.allocs;
+            al.erase(std::remove(al.begin(), al.end(), (void*)c.kr_V), al.end());
+            cudaFree(c.kr_V);
+            c.kr_V = nullptr;
+            c.kr_bytes = 0;
+        }
+        c.kr_V = (double2*)dalloc(c, need);
+        c.kr_bytes = need;
+    }
+    SolveWork W;
+    char* base = (char*)c.kr_V;
+    auto take = [&](size_t bytes) { char* q = base; base += (bytes + 255) / 256 * 256; return q; };
+    W.V = (double2*)take((size_t)(m + 1) * p * N * sizeof(double2));
+    W.w = (double2*)take((size_t)p * N * sizeof(double2));
+    W.r = (double2*)take((size_t)p * N * sizeof(double2));
+    W.e = (double2*)take((size_t)p * N * sizeof(double2));
+    W.Ax = (double2*)take((size_t)p * N * sizeof(double2));
+    W.x32 = (float2*)take((size_t)p * N * sizeof(float2));
+    W.y32 = (float2*)take((size_t)p * N * sizeof(float2));
+    W.part = (double2*)take((size_t)kDotBlocks * p * (m + 1) * sizeof(double2));
+    W.h = (double2*)take((size_t)p * (m + 1) * sizeof(double2));
+    W.scl = (double2*)take((size_t)p * sizeof(double2));
+    Krylov K{c, p, N, m, W.V, W.w, W.h, W.part, W.scl, W.x32, W.y32, st};
+    int mv64 = 0, mv32 = 0, outer = 0;
+    std::vector<int> iters(p, 0);
+    std::vector<double> est;
+    // ||b|| per column
+    VSIE_CUDA(cudaMemcpy2DAsync(W.r, N * sizeof(double2), B, ldb * sizeof(double2),
+                                N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+    VSIE_CUDA(cudaMemcpyAsync(W.w, W.r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> bn2;
+    K.norms(bn2);
+    std::vector<double> bn(p);
+    for (int q = 0; q < p; ++q) {
+        bn[q] = std::sqrt(bn2[q]);
+        if (!std::isfinite(bn[q])) throw Error(VSIE_EBREAKDOWN, "non-finite right-hand side");
+    }
+    auto apply64 = [&](const double2* in, double2* out) {
+        matvec_internal<double>(c, p, in, N, out, N, st);
+    };
+    auto apply32 = [&](const double2* in, double2* out) {
+        k_narrow<<<nblk(N * p), 256, 0, st>>>(in, N, p, W.x32);
+        matvec_internal<float>(c, p, W.x32, N, W.y32, N, st);
+        k_widen<<<nblk(N * p), 256, 0, st>>>(W.y32, N, p, out);
+        VSIE_CUDA(cudaGetLastError());
+    };
+    // x = 0
+    VSIE_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, N * sizeof(double2), p, st));
+    std::vector<double> relres(p, 1.0);
+    if (o.mode == 0) {
+        int cnt = 0;
+        gmres_core(K, W.r, tol, maxit, true, [&](const double2* in, double2* out) { apply64(in, out); },
+                   W.e, iters, est, cnt);
+        mv64 += cnt;
+        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), W.e, N * sizeof(double2),
+                                    N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+    } else {
+        for (outer = 0; outer < max_outer; ++outer) {
+            // r = b - Z64 x
+            VSIE_CUDA(cudaMemcpy2DAsync(W.e, N * sizeof(double2), X, ldx * sizeof(double2),
+                                        N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+            apply64(W.e, W.Ax);
+            ++mv64;
+            k_sub<<<nblk(N * p), 256, 0, st>>>(B, ldb, W.Ax, N, N, p, W.r, N);
+            VSIE_CUDA(cudaGetLastError());
+            VSIE_CUDA(cudaMemcpyAsync(W.w, W.r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            std::vector<double> rn2;
+            K.norms(rn2);
+            bool conv = true;
+            for (int q = 0; q < p; ++q) {
+                relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
+                if (!std::isfinite(relres[q])) throw Error(VSIE_EBREAKDOWN, "non-finite residual");
+                conv = conv && relres[q] <= tol;
+            }
+            if (conv) break;
+            // inner correction to inner_tol (never tighter than the outer target needs)
+            double itol = inner_tol;
+            double worst = 0;
+            for (int q = 0; q < p; ++q) worst = std::max(worst, relres[q]);
+            itol = std::max(itol, 0.5 * tol / std::max(worst, 1e-300));
+            itol = std::min(itol, 0.5);
+            int cnt = 0;
+            int budget = maxit;
+            for (int q = 0; q < p; ++q) budget = std::min(budget, maxit - iters[q]);
+            if (budget <= 0) break;
+            gmres_core(K, W.r, itol, budget, false, apply32, W.e, iters, est, cnt);
+            mv32 += cnt;
+            // x += e
+            std::vector<cdd> onev((size_t)p, 1.0);
+            // X[:, c] += e[:, c]
+            VSIE_CUDA(cudaMemcpyAsync(W.h, onev.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
+            k_basis_update<<<nblk(N * p), 256, 0, st>>>(W.e, 1, N, p, W.h, 1.0, X, ldx);
+            VSIE_CUDA(cudaGetLastError());
+        }
+    }
+    // final true FP64 residual
+    VSIE_CUDA(cudaMemcpy2DAsync(W.e, N * sizeof(double2), X, ldx * sizeof(double2),
+                                N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+    apply64(W.e, W.Ax);
+    ++mv64;
+    k_sub<<<nblk(N * p), 256, 0, st>>>(B, ldb, W.Ax, N, N, p, W.w, N);
+    VSIE_CUDA(cudaGetLastError());
+    std::vector<double> rn2;
+    K.norms(rn2);
+    bool conv = true;
+    for (int q = 0; q < p; ++q) {
+        relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
+        conv = conv && relres[q] <= tol;
+    }
+    VSIE_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+        *info = vsie_solve_info{};
+        for (int q = 0; q < p && q < 64; ++q) {
+            info->iters[q] = iters[q];
+            info->relres[q] = relres[q];
+        }
+        info->outer = outer;
+        info->matvecs64 = mv64;
+        info->matvecs32 = mv32;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    for (int q = 0; q < p; ++q)
+        if (!std::isfinite(relres[q])) throw Error(VSIE_EBREAKDOWN, "non-finite final residual");
+    return conv ? VSIE_OK : VSIE_ENOCONV;
+}
+
+// delta-gap right-hand sides
+__global__ void k_set_entry(double2* B, int64_t ldb, int j, int64_t row, double2 v) {
+    B[(size_t)j * ldb + row] = v;
+}
+
+}  // namespace vsie
+
+using namespace vsie;
+
+extern "C" {
+
+vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t ldb, void* X, int64_t ldx,
+                       double tol, const vsie_solve_opts* opts, vsie_solve_info* info,
+                       vsie_stream stream) {
+    if (!ctx) { set_global_err("null context"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    try {
+        if (!B || !X) throw Error(VSIE_EINVAL, "null B or X");
+        const vsie_status st = solve_impl(*c, p, (const double2*)B, ldb, (double2*)X, ldx, tol, opts,
+                                          info, reinterpret_cast<cudaStream_t>(stream));
+        if (st == VSIE_ENOCONV) c->err = "GMRES reached maxit before the tolerance";
+        return st;
+    } catch (const Error& e) {
+        c->err = e.msg;
+        return e.st;
+    }
+}
+
+vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t* ports, double V, void* B,
+                           int64_t ldb, vsie_stream stream) {
+    if (!ctx) { set_global_err("null context"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    try {
+        if (!B || (nports > 0 && !ports)) throw Error(VSIE_EINVAL, "null B or port list");
+        if (ldb < c->N) throw Error(VSIE_EINVAL, "leading dimension < N");
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        VSIE_CUDA(cudaMemset2DAsync(B, ldb * sizeof(double2), 0, c->N * sizeof(double2), nports, st));
+        for (int j = 0; j < nports; ++j) {
+            const int q = ports[j];
+            if (q < 0 || q >= (int)c->port_row.size()) throw Error(VSIE_EINVAL, "port index out of range");
+            const std::complex<double> v(0.0, c->omega * kEps0 * V * c->port_len[q]);
+            k_set_entry<<<1, 1, 0, st>>>((double2*)B, ldb, j, c->port_row[q], make_double2(v.real(), v.imag()));
+        }
+        VSIE_CUDA(cudaGetLastError());
+    } catch (const Error& e) {
+        c->err = e.msg;
+        return e.st;
+    }
+    return VSIE_OK;
+}
+
+}  // extern "C"

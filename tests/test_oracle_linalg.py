@@ -71,3 +71,21 @@ def test_gmres_vs_lu():
     x2, info2 = gmres.gmres(lambda v: A @ v, b, 1e-10, restart=15, M=lambda v: Mi @ v)
     assert info2["relres"] <= 1e-10 and info2["iters"] < info["iters"]
     assert np.linalg.norm(x2 - xs) / np.linalg.norm(xs) < 1e-9
+
+
+def test_gmres_estimate_equals_true_residual_nonnormal_complex():
+    """Without restarts GMRES is exact in n steps, and its Givens residual
+    estimate equals the true residual at every step (complex, non-normal,
+    indefinite matrix: a wrong rotation convention fails this)."""
+    rng = np.random.default_rng(4)
+    n = 40
+    A = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) + \
+        np.diag(np.exp(2j * np.pi * rng.random(n)))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, info = gmres.gmres(lambda v: A @ v, b, 1e-12, restart=n, maxit=n)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 1e-10
+    # estimate after k steps equals the true residual of the k-step solution
+    for k in (5, 17, 29):
+        xk, ik = gmres.gmres(lambda v: A @ v, b, 1e-30, restart=k, maxit=k)
+        true = np.linalg.norm(A @ xk - b) / np.linalg.norm(b)
+        assert abs(ik["est"] - true) <= 1e-9 * true
