@@ -136,6 +136,8 @@ typedef struct {
     int32_t maxit;      /* total inner iteration cap per RHS (default 2000)               */
     double inner_tol;   /* mode 1: relative tolerance of each inner solve (default 1e-4)  */
     int32_t max_outer;  /* mode 1: refinement steps cap (default 20)                      */
+    int32_t precond;    /* right preconditioner: 0 = block (inverses of the two surface
+                           blocks, inverse body diagonal; default), 1 = none             */
 } vsie_solve_opts;
 
 typedef struct {

@@ -2,6 +2,8 @@
 // GMRES with restart; Saad and Schultz 1986), each RHS with its own Krylov space
 // and one shared multi-RHS matvec per iteration.
 //
+// Both modes apply the block preconditioner of precond.cu on the right
+// (A M y = b, x = M y) unless precond = 1.
 //  mode 0 (plain FP64): GMRES(m), FP64 matvec, classical Gram-Schmidt with one
 //         re-orthogonalisation pass (CGS2), Givens rotations, true residual
 //         recomputed at every restart.
@@ -312,8 +314,8 @@ static void gmres_core(Krylov& K, const double2* r, double tol, int maxit, bool 
 
 struct SolveWork {
     double2 *V = nullptr, *w = nullptr, *h = nullptr, *part = nullptr, *scl = nullptr;
-    double2 *r = nullptr, *e = nullptr, *Ax = nullptr;
-    float2 *x32 = nullptr, *y32 = nullptr;
+    double2 *r = nullptr, *e = nullptr, *Ax = nullptr, *z = nullptr;
+    float2 *x32 = nullptr, *y32 = nullptr, *t32 = nullptr;
 };
 
 vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X, int64_t ldx,
@@ -333,8 +335,10 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t N = c.N;
     // workspace (kept in the context between solves)
-    const size_t need = ((size_t)(m + 1) * p * N + 4 * (size_t)p * N) * sizeof(double2) +
-                        2 * (size_t)p * N * sizeof(float2) +
+    const bool use_pc = o.precond != 1;
+    if (use_pc) build_block_precond(c);
+    const size_t need = ((size_t)(m + 1) * p * N + 5 * (size_t)p * N) * sizeof(double2) +
+                        3 * (size_t)p * N * sizeof(float2) +
                         ((size_t)kDotBlocks * p * (m + 1) + (size_t)p * (m + 1) + p) * sizeof(double2) +
                         16 * 256;   // slack for the 256-byte alignment of each slice below
     if (c.kr_bytes < need) {
@@ -356,8 +360,10 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     W.r = (double2*)take((size_t)p * N * sizeof(double2));
     W.e = (double2*)take((size_t)p * N * sizeof(double2));
     W.Ax = (double2*)take((size_t)p * N * sizeof(double2));
+    W.z = (double2*)take((size_t)p * N * sizeof(double2));
     W.x32 = (float2*)take((size_t)p * N * sizeof(float2));
     W.y32 = (float2*)take((size_t)p * N * sizeof(float2));
+    W.t32 = (float2*)take((size_t)p * N * sizeof(float2));
     W.part = (double2*)take((size_t)kDotBlocks * p * (m + 1) * sizeof(double2));
     W.h = (double2*)take((size_t)p * (m + 1) * sizeof(double2));
     W.scl = (double2*)take((size_t)p * sizeof(double2));
@@ -379,10 +385,39 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     auto apply64 = [&](const double2* in, double2* out) {
         matvec_internal<double>(c, p, in, N, out, N, st);
     };
-    auto apply32 = [&](const double2* in, double2* out) {
+    // right-preconditioned operators A M (FP64) and A32 M32 (FP32 inside)
+    auto apply64_pc = [&](const double2* in, double2* out) {
+        if (!use_pc) { apply64(in, out); return; }
+        apply_block_precond<double>(c, p, in, N, W.z, N, st);
+        apply64(W.z, out);
+    };
+    auto apply32_pc = [&](const double2* in, double2* out) {
         k_narrow<<<nblk(N * p), 256, 0, st>>>(in, N, p, W.x32);
-        matvec_internal<float>(c, p, W.x32, N, W.y32, N, st);
+        const float2* src = W.x32;
+        if (use_pc) {
+            apply_block_precond<float>(c, p, W.x32, N, W.t32, N, st);
+            src = W.t32;
+        }
+        matvec_internal<float>(c, p, src, N, W.y32, N, st);
         k_widen<<<nblk(N * p), 256, 0, st>>>(W.y32, N, p, out);
+        VSIE_CUDA(cudaGetLastError());
+    };
+    // x-space correction M e (FP64 path) and M32 e (refinement path)
+    auto precond64 = [&](const double2* in, double2* out) {
+        if (!use_pc) {
+            VSIE_CUDA(cudaMemcpyAsync(out, in, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            return;
+        }
+        apply_block_precond<double>(c, p, in, N, out, N, st);
+    };
+    auto precond32 = [&](const double2* in, double2* out) {
+        if (!use_pc) {
+            VSIE_CUDA(cudaMemcpyAsync(out, in, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            return;
+        }
+        k_narrow<<<nblk(N * p), 256, 0, st>>>(in, N, p, W.x32);
+        apply_block_precond<float>(c, p, W.x32, N, W.t32, N, st);
+        k_widen<<<nblk(N * p), 256, 0, st>>>(W.t32, N, p, out);
         VSIE_CUDA(cudaGetLastError());
     };
     // x = 0
@@ -390,10 +425,10 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     std::vector<double> relres(p, 1.0);
     if (o.mode == 0) {
         int cnt = 0;
-        gmres_core(K, W.r, tol, maxit, true, [&](const double2* in, double2* out) { apply64(in, out); },
-                   W.e, iters, est, cnt);
+        gmres_core(K, W.r, tol, maxit, true, apply64_pc, W.e, iters, est, cnt);
         mv64 += cnt;
-        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), W.e, N * sizeof(double2),
+        precond64(W.e, W.z);
+        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), W.z, N * sizeof(double2),
                                     N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     } else {
         for (outer = 0; outer < max_outer; ++outer) {
@@ -424,13 +459,13 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             int budget = maxit;
             for (int q = 0; q < p; ++q) budget = std::min(budget, maxit - iters[q]);
             if (budget <= 0) break;
-            gmres_core(K, W.r, itol, budget, false, apply32, W.e, iters, est, cnt);
+            gmres_core(K, W.r, itol, budget, false, apply32_pc, W.e, iters, est, cnt);
             mv32 += cnt;
-            // x += e
+            // x += M e
+            precond32(W.e, W.z);
             std::vector<cdd> onev((size_t)p, 1.0);
-            // X[:, c] += e[:, c]
             VSIE_CUDA(cudaMemcpyAsync(W.h, onev.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
-            k_basis_update<<<nblk(N * p), 256, 0, st>>>(W.e, 1, N, p, W.h, 1.0, X, ldx);
+            k_basis_update<<<nblk(N * p), 256, 0, st>>>(W.z, 1, N, p, W.h, 1.0, X, ldx);
             VSIE_CUDA(cudaGetLastError());
         }
     }

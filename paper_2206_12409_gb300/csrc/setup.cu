@@ -20,11 +20,29 @@
 #include <cmath>
 #include <map>
 #include <numeric>
+#include <chrono>
+#include <cstdio>
 #include <random>
 
 namespace vsie {
 
 using hla::cd;
+
+// Phase timing of the set-up, printed to stderr when built with -DVSIE_TRACE.
+struct PhaseTimer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    void mark(const char* what) {
+#ifdef VSIE_TRACE
+        cudaDeviceSynchronize();
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "[vsie setup] %-28s %8.3f s\n", what,
+                std::chrono::duration<double>(t - t0).count());
+        t0 = t;
+#else
+        (void)what;
+#endif
+    }
+};
 
 vsie_status create_from_parts_impl(const vsie_grid* body, const double* eps_r,
                                    const double* sigma, double freq, const vsie_options* opts,
@@ -269,95 +287,108 @@ static inline double2 d2(cd z) { return make_double2(z.real(), z.imag()); }
 static inline cd cdv(double2 z) { return cd(z.x, z.y); }
 
 // ------------------------------------------------------------------ ACA
-// Partial-pivoting ACA of an m x n matrix whose rows/columns come from
-// callbacks writing into device buffers; Z ~= U V^H with U (m x k) kept on the
-// device (Ud, capacity kmax) and V (n x k) on the host.  Stops when
-// ||u_k|| ||v_k|| <= tol ||Z_k||_F (Zhao et al. 2005).
+// Partial-pivoting ACA of an m x n matrix whose rows/columns are written into
+// device buffers by callbacks; Z ~= U V^H with U (m x k) and V (n x k) kept on
+// the device (capacity kmax columns each).  Stops when ||u_k|| ||v_k|| <=
+// tol ||Z_k||_F with ||Z_k||_F updated recursively (Zhao et al. 2005).  All
+// vector work runs on the GPU; the host only handles scalars.
 struct AcaResult {
     int k = 0;
-    std::vector<cd> V;   // n x k, column-major
 };
+
+__global__ void k_conj_scale(double2* x, int64_t n, double2 s) {
+    // x = conj(x * s)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 t = cmul(x[i], s);
+        x[i] = make_double2(t.x, -t.y);
+    }
+}
 
 template <typename RowF, typename ColF>
 static AcaResult aca_device(Scratch& S, int64_t m, int64_t n, double tol, int kmax, RowF get_row,
-                            ColF get_col, double2* Ud) {
+                            ColF get_col, double2* Ud, double2* Vd) {
+    // Vd columns hold conj(v_k) (so that Z ~= U V^H); the residual row uses
+    // v_k = conj(Vd[:, k]).
     AcaResult out;
-    std::vector<cd> vs;                       // n x k (host), rows of Z ~ sum u v^T: v stored
-    std::vector<uint8_t> used_c(n, 0);
     uint8_t* used_r = (uint8_t*)dalloc(S.c, m);
+    uint8_t* used_c = (uint8_t*)dalloc(S.c, n);
     VSIE_CUDA(cudaMemset(used_r, 0, m));
+    VSIE_CUDA(cudaMemset(used_c, 0, n));
     double2* col = (double2*)dalloc(S.c, m * sizeof(double2));
+    double2* row = (double2*)dalloc(S.c, n * sizeof(double2));
     double2* coef = (double2*)dalloc(S.c, (size_t)std::max(kmax, 1) * sizeof(double2));
     double2* dots = (double2*)dalloc(S.c, (size_t)std::max(kmax, 1) * sizeof(double2));
-    std::vector<cd> row(n), uirow;
-    std::vector<double2> hrow(n);
+    double2* dots2 = (double2*)dalloc(S.c, (size_t)std::max(kmax, 1) * sizeof(double2));
     int64_t i = 0;
     double norm2 = 0.0;
     int k = 0;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+    const uint8_t one_b = 1;
     for (int it = 0; it < kmax && k < kmax; ++it) {
-        const uint8_t one_b = 1;
         VSIE_CUDA(cudaMemcpy(used_r + i, &one_b, 1, cudaMemcpyHostToDevice));
-        get_row(i, hrow.data());
-        for (int64_t j = 0; j < n; ++j) row[j] = cdv(hrow[j]);
-        // residual row: subtract sum_l U[i, l] v_l
+        get_row(i, row);
         if (k > 0) {
-            std::vector<double2> ui(k);
-            VSIE_CUDA(cudaMemcpy2D(ui.data(), sizeof(double2), Ud + i, m * sizeof(double2),
-                                   sizeof(double2), k, cudaMemcpyDeviceToHost));
-            for (int l = 0; l < k; ++l) {
-                const cd u = cdv(ui[l]);
-                const cd* v = &vs[(size_t)n * l];
-                for (int64_t j = 0; j < n; ++j) row[j] -= u * v[j];
-            }
+            // row -= sum_l U[i, l] v_l,  v_l = conj(Vd[:, l]):
+            //   conj(row) -= Vd[:, :k] conj(U[i, :k])
+            VSIE_CUDA(cudaMemcpy2D(coef, sizeof(double2), Ud + i, m * sizeof(double2),
+                                   sizeof(double2), k, cudaMemcpyDeviceToDevice));
+            k_conj_scale<<<64, 256>>>(row, n, one);             // row <- conj(row)
+            k_conj_scale<<<1, 256>>>(coef, k, one);             // coef <- conj(U[i, :])
+            cgemm<double>(S.c, OP_N, (int)n, 1, k, mone, Vd, n, 0, coef, k, 0, one, row, n, 0, 1,
+                          nullptr, nullptr, 0);
+            k_conj_scale<<<64, 256>>>(row, n, one);             // back to row
+            VSIE_CUDA(cudaGetLastError());
         }
-        int64_t jm = -1;
-        double best = -1;
-        for (int64_t j = 0; j < n; ++j)
-            if (!used_c[j] && std::norm(row[j]) > best) { best = std::norm(row[j]); jm = j; }
-        if (jm < 0 || best == 0.0) {
+        int64_t jm;
+        double rn2;
+        absmax(S, row, n, used_c, jm, rn2);
+        double2 piv = make_double2(0, 0);
+        if (jm >= 0) VSIE_CUDA(cudaMemcpy(&piv, row + jm, sizeof(double2), cudaMemcpyDeviceToHost));
+        if (jm < 0 || (piv.x == 0.0 && piv.y == 0.0)) {
             // zero residual row: try the next unused row
-            bool found = false;
             std::vector<uint8_t> ur(m);
             VSIE_CUDA(cudaMemcpy(ur.data(), used_r, m, cudaMemcpyDeviceToHost));
-            for (int64_t q = 0; q < m; ++q)
-                if (!ur[q]) { i = q; found = true; break; }
-            if (!found) break;
+            int64_t q = 0;
+            while (q < m && ur[q]) ++q;
+            if (q == m) break;
+            i = q;
             continue;
         }
-        used_c[jm] = 1;
-        const cd piv = row[jm];
-        for (int64_t j = 0; j < n; ++j) row[j] /= piv;     // v
-        // residual column
+        VSIE_CUDA(cudaMemcpy(used_c + jm, &one_b, 1, cudaMemcpyHostToDevice));
+        // v = row / piv, stored conjugated in Vd[:, k]
+        const cd ip = 1.0 / cdv(piv);
+        VSIE_CUDA(cudaMemcpy(Vd + (size_t)n * k, row, n * sizeof(double2), cudaMemcpyDeviceToDevice));
+        k_conj_scale<<<64, 256>>>(Vd + (size_t)n * k, n, d2(ip));
+        // residual column: col -= U[:, :k] v[jm, :k],  v_l[jm] = conj(Vd[jm, l])
         get_col(jm, col);
         if (k > 0) {
-            std::vector<double2> vj(k);
-            for (int l = 0; l < k; ++l) vj[l] = d2(vs[(size_t)n * l + jm]);
-            VSIE_CUDA(cudaMemcpy(coef, vj.data(), k * sizeof(double2), cudaMemcpyHostToDevice));
+            VSIE_CUDA(cudaMemcpy2D(coef, sizeof(double2), Vd + jm, n * sizeof(double2),
+                                   sizeof(double2), k, cudaMemcpyDeviceToDevice));
+            k_conj_scale<<<1, 256>>>(coef, k, one);
             cgemm<double>(S.c, OP_N, (int)m, 1, k, mone, Ud, m, 0, coef, k, 0, one, col, m, 0, 1,
                           nullptr, nullptr, 0);
         }
-        // u = col; norms and cross terms
+        VSIE_CUDA(cudaGetLastError());
         int64_t inext;
         double nu2;
         absmax(S, col, m, used_r, inext, nu2);
-        double nv2 = 0;
-        for (int64_t j = 0; j < n; ++j) nv2 += std::norm(row[j]);
+        int64_t dummy;
+        double nv2;
+        absmax(S, Vd + (size_t)n * k, n, nullptr, dummy, nv2);
         double cross = 0.0;
         if (k > 0) {
+            // (u_l^H u)(v_l^H v) with v = conj(Vd): v_l^H v = conj(Vd_l^H Vd_k)
             cgemm<double>(S.c, OP_H, k, 1, (int)m, one, Ud, m, 0, col, m, 0, zero, dots, k, 0, 1,
                           nullptr, nullptr, 0);
-            std::vector<double2> hd(k);
-            VSIE_CUDA(cudaMemcpy(hd.data(), dots, k * sizeof(double2), cudaMemcpyDeviceToHost));
-            for (int l = 0; l < k; ++l) {
-                cd vv = 0.0;
-                const cd* v = &vs[(size_t)n * l];
-                for (int64_t j = 0; j < n; ++j) vv += std::conj(v[j]) * row[j];
-                cross += 2.0 * std::real(cdv(hd[l]) * vv);
-            }
+            cgemm<double>(S.c, OP_H, k, 1, (int)n, one, Vd, n, 0, Vd + (size_t)n * k, n, 0, zero,
+                          dots2, k, 0, 1, nullptr, nullptr, 0);
+            std::vector<double2> a(k), b(k);
+            VSIE_CUDA(cudaMemcpy(a.data(), dots, k * sizeof(double2), cudaMemcpyDeviceToHost));
+            VSIE_CUDA(cudaMemcpy(b.data(), dots2, k * sizeof(double2), cudaMemcpyDeviceToHost));
+            for (int l = 0; l < k; ++l) cross += 2.0 * std::real(cdv(a[l]) * std::conj(cdv(b[l])));
         }
         VSIE_CUDA(cudaMemcpy(Ud + (size_t)m * k, col, m * sizeof(double2), cudaMemcpyDeviceToDevice));
-        vs.insert(vs.end(), row.begin(), row.end());
         ++k;
         norm2 += cross + nu2 * nv2;
         if (std::sqrt(nu2 * nv2) <= tol * std::sqrt(std::max(norm2, 0.0))) break;
@@ -365,9 +396,6 @@ static AcaResult aca_device(Scratch& S, int64_t m, int64_t n, double tol, int km
         i = inext;
     }
     out.k = k;
-    out.V.resize((size_t)n * k);
-    for (int l = 0; l < k; ++l)
-        for (int64_t j = 0; j < n; ++j) out.V[(size_t)n * l + j] = std::conj(vs[(size_t)n * l + j]);
     return out;
 }
 
@@ -536,6 +564,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
 
     Scratch S;
     VSIE_CUDA(cudaGetDevice(&S.c.device));
+    PhaseTimer T;
     Built B;
     MeshHost mh_c, mh_s;
     MeshDev md_c, md_s;
@@ -543,6 +572,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
     if (has_c) { mh_c = build_rwg(*coil); md_c = upload_mesh(S.c, mh_c); }
     if (has_s) { mh_s = build_rwg(*shield); md_s = upload_mesh(S.c, mh_s); }
     const int m_n = has_c ? mh_c.m : 0, m_f = has_s ? mh_s.m : 0;
+    T.mark("meshes");
     const int s3 = s * s * s;
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     GridDev gb;
@@ -604,6 +634,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         cgemm<double>(S.c, OP_N, 3 * s3, m_n, 3 * Nc, one, dX, 3 * s3, 0, E, 3 * Nc, 0, zero, dW,
                       3 * s3, 0, 1, nullptr, nullptr, 0);
         B.W = to_host(dW, (size_t)3 * s3 * m_n);   // column n = row n of W (3 s3 per RWG)
+        T.mark("pFFT projection");
 
         // --- precorrection on near pairs
         std::vector<std::vector<std::pair<int32_t, cd>>> rows(3 * (size_t)n_b);
@@ -663,6 +694,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             }
         }
 
+        T.mark("precorrection");
         // --- direct near block and the grid part P^T K P
         double2* Knn = (double2*)dalloc(S.c, (size_t)m_n * m_n * sizeof(double2));
         efie_block(md_c, md_c, true, m_n, nullptr, m_n, nullptr, k0, -1.0, Knn, m_n);
@@ -710,30 +742,34 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             destroy_ctx(tc);
         }
         B.Znn = std::move(Znn);
+        T.mark("near block");
     }
 
     if (has_s) {
         // --- far-far dense block (device, FP64)
         B.dZff = (double2*)dalloc(S.c, (size_t)m_f * m_f * sizeof(double2));
         efie_block(md_s, md_s, true, m_f, nullptr, m_f, nullptr, k0, -1.0, B.dZff, m_f);
+        T.mark("far-far block");
         // --- near-far block by ACA
         if (has_c) {
             double2* Zfn = (double2*)dalloc(S.c, (size_t)m_n * m_f * sizeof(double2));
             efie_block(md_c, md_s, false, m_n, nullptr, m_f, nullptr, k0, -1.0, Zfn, m_n);
             const int kmax = std::min(m_n, m_f);
             double2* Ud = (double2*)dalloc(S.c, (size_t)m_n * std::max(kmax, 1) * sizeof(double2));
+            double2* Vd = (double2*)dalloc(S.c, (size_t)m_f * std::max(kmax, 1) * sizeof(double2));
             auto row = [&](int64_t i, double2* dst) {
                 VSIE_CUDA(cudaMemcpy2D(dst, sizeof(double2), Zfn + i, m_n * sizeof(double2),
-                                       sizeof(double2), m_f, cudaMemcpyDeviceToHost));
+                                       sizeof(double2), m_f, cudaMemcpyDeviceToDevice));
             };
             auto colf = [&](int64_t j, double2* dst) {
                 VSIE_CUDA(cudaMemcpy(dst, Zfn + (size_t)m_n * j, m_n * sizeof(double2),
                                      cudaMemcpyDeviceToDevice));
             };
-            AcaResult ar = aca_device(S, m_n, m_f, aca_tol, kmax, row, colf, Ud);
+            AcaResult ar = aca_device(S, m_n, m_f, aca_tol, kmax, row, colf, Ud, Vd);
             B.aca_rank = ar.k;
             B.U = to_host(Ud, (size_t)m_n * ar.k);
-            B.V = std::move(ar.V);
+            B.V = to_host(Vd, (size_t)m_f * ar.k);
+            T.mark("near-far ACA");
         }
         // --- TT of the far coupling, per component
         const int kmax = (int)std::min<int64_t>({(int64_t)m_f, n_b, (int64_t)1024});
@@ -742,12 +778,13 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         int64_t* dvox1 = (int64_t*)dalloc(S.c, sizeof(int64_t));
         int* dcol1 = (int*)dalloc(S.c, sizeof(int));
         double2* Ud = (double2*)dalloc(S.c, (size_t)n_b * kmax * sizeof(double2));
+        double2* Vall = (double2*)dalloc(S.c, (size_t)m_f * kmax * sizeof(double2));
         for (int a = 0; a < 3; ++a) {
             auto row = [&](int64_t v, double2* dst) {
                 VSIE_CUDA(cudaMemcpy(dvox1, &v, sizeof(int64_t), cudaMemcpyHostToDevice));
                 coupling_block(md_s, gb, 1, dvox1, m_f, nullptr, k0, false, -1.0, rowbuf, 1, m_f);
                 VSIE_CUDA(cudaMemcpy(dst, rowbuf + (size_t)a * m_f, m_f * sizeof(double2),
-                                     cudaMemcpyDeviceToHost));
+                                     cudaMemcpyDeviceToDevice));
             };
             auto colf = [&](int64_t j, double2* dst) {
                 const int jj = (int)j;
@@ -758,15 +795,12 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             };
             // the ACA stopping test is a heuristic that can overshoot its tolerance by a
             // few times; tol / 10 leaves the TT-SVD half of the budget
-            AcaResult ar = aca_device(S, n_b, m_f, tt_tol / 10, kmax, row, colf, Ud);
+            AcaResult ar = aca_device(S, n_b, m_f, tt_tol / 10, kmax, row, colf, Ud, Vall);
             const int k = ar.k;
+            T.mark("TT cross (ACA)");
             // orthonormalise V (m_f x k) by Cholesky QR, twice: V = Q R; U' = U R^H
             double2* Vd = (double2*)dalloc(S.c, (size_t)m_f * k * sizeof(double2));
-            {
-                std::vector<double2> hv(ar.V.size());
-                for (size_t i = 0; i < hv.size(); ++i) hv[i] = d2(ar.V[i]);
-                VSIE_CUDA(cudaMemcpy(Vd, hv.data(), hv.size() * sizeof(double2), cudaMemcpyHostToDevice));
-            }
+            VSIE_CUDA(cudaMemcpy(Vd, Vall, (size_t)m_f * k * sizeof(double2), cudaMemcpyDeviceToDevice));
             double2* Up = (double2*)dalloc(S.c, (size_t)n_b * k * sizeof(double2));
             VSIE_CUDA(cudaMemcpy(Up, Ud, (size_t)n_b * k * sizeof(double2), cudaMemcpyDeviceToDevice));
             double2* Gk = (double2*)dalloc(S.c, (size_t)k * k * sizeof(double2));
@@ -812,6 +846,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             B.tt[a][1] = to_host(f2.L, (size_t)r1 * nb[1] * r2);
             B.tt[a][2] = to_host(f3.L, (size_t)r2 * nb[2] * r3);
             B.tt[a][3] = to_host(G4, (size_t)r3 * m_f);
+            T.mark("TT-SVD");
         }
     }
     VSIE_CUDA(cudaDeviceSynchronize());
@@ -844,6 +879,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
     Ctx* c = nullptr;
     vsie_status st = create_from_parts_impl(body, eps_r, sigma, freq, &fo, &P, B.dZff, &c);
     if (st != VSIE_OK) throw Error(st, "context creation from the set-up parts failed");
+    T.mark("context");
     if (B.dZff) {   // the context now owns the far-far block
         auto& al = S.c.allocs;
         al.erase(std::remove(al.begin(), al.end(), (void*)B.dZff), al.end());

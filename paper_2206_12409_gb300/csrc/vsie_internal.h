@@ -119,6 +119,9 @@ struct OpData {
     cx<R>* t4 = nullptr;
     cx<R>* splitk = nullptr;    // split-K partial sums
     size_t splitk_elems = 0;
+    cx<R>* pc_Zffi = nullptr;   // block preconditioner: Z_ff^-1 (m_f x m_f)
+    cx<R>* pc_Znni = nullptr;   // Z_nn^-1 (m_n x m_n)
+    cx<R>* pc_bdiag = nullptr;  // inverse body diagonal (n_b)
     int tune[5] = {0, 0, 0, 0, 0};     // chosen FFT pass variants (autotuned)
     float tune_ms[5][8] = {{0}};       // measured time per variant (ms, p = min(max_rhs, 4))
     bool ready = false;
@@ -182,6 +185,7 @@ struct Ctx {
     size_t kr_bytes = 0;
     bool owns_all = true;
     double2* dZff_in = nullptr;        // far-far block handed over on the device (FP64)
+    bool pc_ready = false;             // block preconditioner built
     vsie_parts parts_view{};           // filled by vsie_get_parts
     std::vector<std::complex<double>> hZff_copy;
 };
@@ -223,6 +227,10 @@ template <typename R>
 void conv_set_attrs();
 template <typename R>
 void conv_autotune(Ctx& c);
+void build_block_precond(Ctx& c);
+template <typename R>
+void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
+                         cudaStream_t st);
 template <typename R>
 void upload_twiddles(Ctx& c);
 

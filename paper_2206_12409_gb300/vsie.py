@@ -61,7 +61,7 @@ class vsie_parts(C.Structure):
 
 class vsie_solve_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("restart", C.c_int32), ("maxit", C.c_int32),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int32)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("precond", C.c_int32)]
 
 
 class vsie_solve_info(C.Structure):
