@@ -205,6 +205,20 @@ VSIE_API vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t
                        int64_t ldx, double tol, const vsie_solve_opts* opts,
                        vsie_solve_info* info, vsie_stream stream);
 
+/* Profiling.  vsie_profile(ctx, 1) clears the counters and starts recording a
+ * CUDA event pair around every kernel group launched by calls on the context
+ * (0 stops recording; launch counts are always kept).  vsie_profile_query
+ * synchronises the device and returns, for a group, the summed event time in
+ * ms, the number of kernel launches and the algorithmic bytes moved (defined
+ * for group 0 only: 54 complex values per extended-grid voxel and RHS plus the
+ * spectrum octants).  Groups: 0 FFT convolution (K1), 1 pFFT projection and
+ * interpolation, 2 precorrection, 3 dense and low-rank surface blocks, 4 TT
+ * chain, 5 Krylov vector kernels, 6 block preconditioner; group -1 returns the
+ * launches of all groups. */
+VSIE_API vsie_status vsie_profile(vsie_ctx* ctx, int32_t enable);
+VSIE_API vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms, int64_t* launches,
+                                        double* alg_bytes);
+
 /* Write the context's operator (grid, materials, frequency, options, parts) to
  * a versioned binary file; vsie_load recreates a context from it (Sec. VI:
  * compressed coupling matrices stored and reused). */

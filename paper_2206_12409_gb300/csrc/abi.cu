@@ -417,6 +417,8 @@ vsie_status fail(Ctx* c, const Error& e) {
 
 void destroy_ctx(Ctx* c) {
     if (!c) return;
+    for (int g = 0; g < PG_N; ++g)
+        for (auto& e : c->prof.ev[g]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -564,6 +566,47 @@ vsie_status vsie_get_parts(vsie_ctx* ctx, vsie_parts* parts) {
     } catch (const Error& e) {
         return fail(c, e);
     }
+    return VSIE_OK;
+}
+
+vsie_status vsie_profile(vsie_ctx* ctx, int32_t enable) {
+    if (!ctx) { set_global_err("null context"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (enable) {
+        cudaDeviceSynchronize();
+        for (int g = 0; g < PG_N; ++g) {
+            for (auto& e : c->prof.ev[g]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+            c->prof.ev[g].clear();
+            c->prof.launches[g] = 0;
+            c->prof.alg_bytes[g] = 0;
+        }
+    }
+    c->prof.on = enable != 0;
+    return VSIE_OK;
+}
+
+vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms, int64_t* launches,
+                               double* alg_bytes) {
+    if (!ctx) { set_global_err("null context"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (group < -1 || group >= PG_N) { c->err = "unknown profiling group"; return VSIE_EINVAL; }
+    if (group == -1) {
+        int64_t s = 0;
+        for (int g = 0; g < PG_N; ++g) s += c->prof.launches[g];
+        if (launches) *launches = s;
+        if (ms) *ms = 0;
+        if (alg_bytes) *alg_bytes = 0;
+        return VSIE_OK;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) { c->err = "device error"; return VSIE_ECUDA; }
+    double t = 0;
+    for (auto& e : c->prof.ev[group]) {
+        float f = 0;
+        if (cudaEventElapsedTime(&f, e.first, e.second) == cudaSuccess) t += f;
+    }
+    if (ms) *ms = t;
+    if (launches) *launches = c->prof.launches[group];
+    if (alg_bytes) *alg_bytes = c->prof.alg_bytes[group];
     return VSIE_OK;
 }
 

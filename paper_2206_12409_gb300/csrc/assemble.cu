@@ -318,11 +318,12 @@ __device__ void gop_rwg(const MeshDev& m, int n, V3 r, int rule, double k0, doub
     }
 }
 
-// Coupling block: out[a][iv + nvx * ic] (component-major planes of nvx x nc,
-// plane stride pstride) = sign * K[(vox[iv], a), cols[ic]]
+// Coupling block: out[a][iv + ldo * ic] (component-major planes, plane stride
+// pstride) = sign * K[(vox[iv], a), cols[ic]]; with only >= 0 just that
+// component is written, at out[iv + ldo * ic].
 __global__ void k_coupling(MeshDev m, GridDev g, int nvx, const int64_t* __restrict__ vox, int nc,
                            const int* __restrict__ cols, double k0, bool near, double sign,
-                           double2* __restrict__ out, int64_t ldo, int64_t pstride) {
+                           double2* __restrict__ out, int64_t ldo, int64_t pstride, int only) {
     const int64_t tot = (int64_t)nvx * nc;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -347,8 +348,12 @@ __global__ void k_coupling(MeshDev m, GridDev g, int nvx, const int64_t* __restr
             gop_rwg(m, n, c, 0, k0, acc);
         }
         const double h3 = g.h * g.h * g.h * sign;
-        for (int a = 0; a < 3; ++a)
-            out[(size_t)a * pstride + (size_t)iv + (size_t)ic * ldo] = cscale(acc[a], h3);
+        if (only >= 0) {
+            out[(size_t)iv + (size_t)ic * ldo] = cscale(acc[only], h3);
+        } else {
+            for (int a = 0; a < 3; ++a)
+                out[(size_t)a * pstride + (size_t)iv + (size_t)ic * ldo] = cscale(acc[a], h3);
+        }
     }
 }
 
@@ -381,11 +386,11 @@ void efie_block(const MeshDev& ma, const MeshDev& mb, bool same, int nr, const i
 
 void coupling_block(const MeshDev& m, const GridDev& g, int nvx, const int64_t* vox, int nc,
                     const int* cols, double k0, bool near, double sign, double2* out, int64_t ldo,
-                    int64_t pstride) {
+                    int64_t pstride, int only) {
     upload_rules();
     if ((int64_t)nvx * nc == 0) return;
     k_coupling<<<grid_for((int64_t)nvx * nc), 128>>>(m, g, nvx, vox, nc, cols, k0, near, sign, out,
-                                                      ldo, pstride);
+                                                      ldo, pstride, only);
     VSIE_CUDA(cudaGetLastError());
 }
 

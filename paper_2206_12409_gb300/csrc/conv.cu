@@ -428,8 +428,14 @@ template <typename R>
 void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
                 cudaStream_t st) {
     const ConvArgs<R> a = make_args<R>(c, X, ldx, Y, ldy);
+    // algorithmic bytes of one launch group: the three-pass schedule moves
+    // 54 n_v complex values per RHS, plus the 6 spectrum octants once
+    const double cs = sizeof(cx<R>);
+    const double alg = 54.0 * (double)c.n_e * cs * p + 6.0 * (double)c.Lh[0] * c.Lh[1] * c.Lh[2] * cs;
+    ProfScope ps(c, PG_FFTCONV, st, alg);
     const int* tune = data<R>(c).tune;
     for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, p, pass, tune[pass], st);
+    prof_count(c, 5);
     VSIE_CUDA(cudaGetLastError());
 }
 

@@ -148,6 +148,7 @@ static void launch(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> al
         if ((size_t)splits * batch * M * N > d.splitk_elems) splits = 1;
     }
     dim3 g(tm, tn, batch * splits);
+    prof_count(c, splits > 1 ? 2 : 1);
     k_cgemm<R, BM, BN, TM, TN><<<g, 256, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB,
                                                   beta, C, ldc, sC, batch, splits, maskB, maskC,
                                                   d.splitk);

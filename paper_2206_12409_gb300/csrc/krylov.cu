@@ -150,6 +150,8 @@ struct Krylov {
 
     // h[c][i] = V_i^H w for i < nvec (device h), copied to host hh
     void dots(int nvec, std::vector<std::complex<double>>& hh) {
+        ProfScope ps(c, PG_KRYLOV, st);
+        prof_count(c, 2);
         dim3 g(kDotBlocks, p, (nvec + kDotGroup - 1) / kDotGroup);
         k_block_dot<<<g, 256, 0, st>>>(V, nvec, N, p, w, N, part);
         k_reduce_dots<<<(p * nvec + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, nvec, h);
@@ -160,6 +162,8 @@ struct Krylov {
     }
     // squared norms of the columns of w
     void norms(std::vector<double>& nn) {
+        ProfScope ps(c, PG_KRYLOV, st);
+        prof_count(c, 2);
         // w against itself: treat w as a one-vector basis
         dim3 g(kDotBlocks, p, 1);
         k_block_dot<<<g, 256, 0, st>>>(w, 1, N, p, w, N, part);
@@ -173,12 +177,16 @@ struct Krylov {
     }
     void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, double2* tgt,
                 int64_t ld) {
+        ProfScope ps(c, PG_KRYLOV, st);
+        prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(h, hh.data(), (size_t)p * nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
         k_basis_update<<<nblk(N * p), 256, 0, st>>>(V, nvec, N, p, h, sgn, tgt, ld);
         VSIE_CUDA(cudaGetLastError());
     }
     void scale_into(const double2* src, int64_t lds, const std::vector<std::complex<double>>& s,
                     double2* dst, int64_t ldd) {
+        ProfScope ps(c, PG_KRYLOV, st);
+        prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(scl, s.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
         k_scale_cols<<<nblk(N * p), 256, 0, st>>>(src, lds, N, p, scl, dst, ldd);
         VSIE_CUDA(cudaGetLastError());

@@ -174,6 +174,8 @@ template <typename R>
 void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
                          cudaStream_t st) {
     OpData<R>& d = data<R>(c);
+    ProfScope ps(c, PG_PRECOND, st);
+    prof_count(c, 1);
     const cx<R> one = mk<cx<R>>(1, 0), zero = mk<cx<R>>(0, 0);
     if (c.m_f > 0)
         cgemm<R>(c, OP_N, c.m_f, p, c.m_f, one, d.pc_Zffi, c.m_f, 0, X, ldx, 0, zero, Y, ldy, 0, 1,

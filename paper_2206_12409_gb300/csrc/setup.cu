@@ -16,6 +16,8 @@
 #include "setup.h"
 #include "hostla.h"
 
+#include <cusolverDn.h>
+
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -294,6 +296,7 @@ static inline cd cdv(double2 z) { return cd(z.x, z.y); }
 // vector work runs on the GPU; the host only handles scalars.
 struct AcaResult {
     int k = 0;
+    std::vector<int64_t> rows, cols;   // pivot row / column of each cross
 };
 
 __global__ void k_conj_scale(double2* x, int64_t n, double2 s) {
@@ -356,6 +359,8 @@ static AcaResult aca_device(Scratch& S, int64_t m, int64_t n, double tol, int km
             continue;
         }
         VSIE_CUDA(cudaMemcpy(used_c + jm, &one_b, 1, cudaMemcpyHostToDevice));
+        out.rows.push_back(i);
+        out.cols.push_back(jm);
         // v = row / piv, stored conjugated in Vd[:, k]
         const cd ip = 1.0 / cdv(piv);
         VSIE_CUDA(cudaMemcpy(Vd + (size_t)n * k, row, n * sizeof(double2), cudaMemcpyDeviceToDevice));
@@ -512,6 +517,26 @@ static Factor truncate(Scratch& S, const double2* A, int m, int c, double delta2
         F.R = Fb.R;
         return F;
     }
+}
+
+// In-place inverse of a small n x n FP64 complex matrix on the device (LU).
+static void invert_f64(Scratch& S, double2* A, int n) {
+    cusolverDnHandle_t h = nullptr;
+    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) throw Error(VSIE_ECUDA, "cusolverDnCreate");
+    int lwork = 0;
+    cusolverDnZgetrf_bufferSize(h, n, n, (cuDoubleComplex*)A, n, &lwork);
+    cuDoubleComplex* work = (cuDoubleComplex*)dalloc(S.c, (size_t)std::max(lwork, 1) * sizeof(double2));
+    int* ipiv = (int*)dalloc(S.c, (size_t)n * sizeof(int));
+    int* info = (int*)dalloc(S.c, sizeof(int));
+    double2* B = (double2*)dalloc(S.c, (size_t)n * n * sizeof(double2));
+    std::vector<double2> I((size_t)n * n, make_double2(0, 0));
+    for (int i = 0; i < n; ++i) I[i + (size_t)n * i] = make_double2(1, 0);
+    VSIE_CUDA(cudaMemcpy(B, I.data(), I.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    const bool ok = cusolverDnZgetrf(h, n, n, (cuDoubleComplex*)A, n, work, ipiv, info) == CUSOLVER_STATUS_SUCCESS &&
+                    cusolverDnZgetrs(h, CUBLAS_OP_N, n, n, (cuDoubleComplex*)A, n, ipiv, (cuDoubleComplex*)B, n, info) == CUSOLVER_STATUS_SUCCESS;
+    cusolverDnDestroy(h);
+    if (!ok) throw Error(VSIE_ECUDA, "skeleton core inversion failed");
+    VSIE_CUDA(cudaMemcpy(A, B, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice));
 }
 
 static std::vector<cd> to_host(const double2* d, size_t n) {
@@ -771,43 +796,80 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             B.V = to_host(Vd, (size_t)m_f * ar.k);
             T.mark("near-far ACA");
         }
-        // --- TT of the far coupling, per component
-        const int kmax = (int)std::min<int64_t>({(int64_t)m_f, n_b, (int64_t)1024});
-        double2* rowbuf = (double2*)dalloc(S.c, (size_t)3 * m_f * sizeof(double2));
-        double2* colbuf = (double2*)dalloc(S.c, (size_t)3 * n_b * sizeof(double2));
+        // --- TT of the far coupling, per component.  Cross approximation: ACA on a
+        // sub-sample of the voxels (every `st`-th voxel per axis, ends included)
+        // picks the pivot voxels I and far RWG J; the skeleton
+        //   Z ~= Z[:, J] Z[I, J]^-1 Z[I, :]
+        // is then formed over all voxels (U = Z[:, J], V^H = Z[I, J]^-1 Z[I, :]).
+        int stv = 1;
+        while ((int64_t)((nb[0] + stv - 1) / stv) * ((nb[1] + stv - 1) / stv) * ((nb[2] + stv - 1) / stv) > 32768) ++stv;
+        std::vector<int> axis_idx[3];
+        for (int d = 0; d < 3; ++d) {
+            for (int i = 0; i < nb[d]; i += stv) axis_idx[d].push_back(i);
+            if (axis_idx[d].back() != nb[d] - 1) axis_idx[d].push_back(nb[d] - 1);
+        }
+        std::vector<int64_t> sub;
+        for (int z : axis_idx[2])
+            for (int y : axis_idx[1])
+                for (int x : axis_idx[0]) sub.push_back(x + (int64_t)nb[0] * (y + (int64_t)nb[1] * z));
+        const int64_t ns = (int64_t)sub.size();
+        int64_t* dsub = up(S.c, sub);
+        const int kmax = (int)std::min<int64_t>({(int64_t)m_f, ns, (int64_t)2048});
         int64_t* dvox1 = (int64_t*)dalloc(S.c, sizeof(int64_t));
         int* dcol1 = (int*)dalloc(S.c, sizeof(int));
-        double2* Ud = (double2*)dalloc(S.c, (size_t)n_b * kmax * sizeof(double2));
-        double2* Vall = (double2*)dalloc(S.c, (size_t)m_f * kmax * sizeof(double2));
         for (int a = 0; a < 3; ++a) {
-            auto row = [&](int64_t v, double2* dst) {
+            Scratch L;   // per-component temporaries, freed at the end of the iteration
+            double2* rowbuf = (double2*)dalloc(L.c, (size_t)m_f * sizeof(double2));
+            double2* colbuf = (double2*)dalloc(L.c, (size_t)ns * sizeof(double2));
+            double2* Usub = (double2*)dalloc(L.c, (size_t)ns * kmax * sizeof(double2));
+            double2* Vall = (double2*)dalloc(L.c, (size_t)m_f * kmax * sizeof(double2));
+            auto row = [&](int64_t i, double2* dst) {
+                const int64_t v = sub[i];
                 VSIE_CUDA(cudaMemcpy(dvox1, &v, sizeof(int64_t), cudaMemcpyHostToDevice));
-                coupling_block(md_s, gb, 1, dvox1, m_f, nullptr, k0, false, -1.0, rowbuf, 1, m_f);
-                VSIE_CUDA(cudaMemcpy(dst, rowbuf + (size_t)a * m_f, m_f * sizeof(double2),
-                                     cudaMemcpyDeviceToDevice));
+                coupling_block(md_s, gb, 1, dvox1, m_f, nullptr, k0, false, -1.0, rowbuf, 1, m_f, a);
+                VSIE_CUDA(cudaMemcpy(dst, rowbuf, m_f * sizeof(double2), cudaMemcpyDeviceToDevice));
             };
             auto colf = [&](int64_t j, double2* dst) {
                 const int jj = (int)j;
                 VSIE_CUDA(cudaMemcpy(dcol1, &jj, sizeof(int), cudaMemcpyHostToDevice));
-                coupling_block(md_s, gb, (int)n_b, nullptr, 1, dcol1, k0, false, -1.0, colbuf, n_b, n_b);
-                VSIE_CUDA(cudaMemcpy(dst, colbuf + (size_t)a * n_b, n_b * sizeof(double2),
-                                     cudaMemcpyDeviceToDevice));
+                coupling_block(md_s, gb, (int)ns, dsub, 1, dcol1, k0, false, -1.0, colbuf, ns, ns, a);
+                VSIE_CUDA(cudaMemcpy(dst, colbuf, ns * sizeof(double2), cudaMemcpyDeviceToDevice));
             };
             // the ACA stopping test is a heuristic that can overshoot its tolerance by a
             // few times; tol / 10 leaves the TT-SVD half of the budget
-            AcaResult ar = aca_device(S, n_b, m_f, tt_tol / 10, kmax, row, colf, Ud, Vall);
+            AcaResult ar = aca_device(L, ns, m_f, tt_tol / 10, kmax, row, colf, Usub, Vall);
             const int k = ar.k;
             T.mark("TT cross (ACA)");
+            // skeleton over all voxels
+            std::vector<int> J(ar.cols.begin(), ar.cols.end());
+            std::vector<int64_t> Ivox(k);
+            for (int l = 0; l < k; ++l) Ivox[l] = sub[ar.rows[l]];
+            int* dJ = up(L.c, J);
+            int64_t* dI = up(L.c, Ivox);
+            double2* Ud = (double2*)dalloc(L.c, (size_t)n_b * k * sizeof(double2));      // Z[:, J]
+            coupling_block(md_s, gb, (int)n_b, nullptr, k, dJ, k0, false, -1.0, Ud, n_b, 0, a);
+            double2* Ra = (double2*)dalloc(L.c, (size_t)k * m_f * sizeof(double2));      // Z[I, :]
+            coupling_block(md_s, gb, k, dI, m_f, nullptr, k0, false, -1.0, Ra, k, 0, a);
+            // core Z[I, J] (k x k) = columns J of Ra, then its inverse
+            double2* Sk = (double2*)dalloc(L.c, (size_t)k * k * sizeof(double2));
+            for (int l = 0; l < k; ++l)
+                VSIE_CUDA(cudaMemcpy(Sk + (size_t)k * l, Ra + (size_t)k * J[l], k * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice));
+            invert_f64(L, Sk, k);
+            // V = (Z[I,J]^-1 Z[I,:])^H = Ra^H Sk^-H   (m_f x k)
+            cgemm2<double>(L.c, OP_H, OP_H, m_f, k, k, one, Ra, k, 0, Sk, k, 0, zero, Vall, m_f, 0, 1,
+                           nullptr, nullptr, 0);
+            T.mark("TT skeleton");
             // orthonormalise V (m_f x k) by Cholesky QR, twice: V = Q R; U' = U R^H
-            double2* Vd = (double2*)dalloc(S.c, (size_t)m_f * k * sizeof(double2));
+            double2* Vd = (double2*)dalloc(L.c, (size_t)m_f * k * sizeof(double2));
             VSIE_CUDA(cudaMemcpy(Vd, Vall, (size_t)m_f * k * sizeof(double2), cudaMemcpyDeviceToDevice));
-            double2* Up = (double2*)dalloc(S.c, (size_t)n_b * k * sizeof(double2));
+            double2* Up = (double2*)dalloc(L.c, (size_t)n_b * k * sizeof(double2));
             VSIE_CUDA(cudaMemcpy(Up, Ud, (size_t)n_b * k * sizeof(double2), cudaMemcpyDeviceToDevice));
-            double2* Gk = (double2*)dalloc(S.c, (size_t)k * k * sizeof(double2));
-            double2* Rk = (double2*)dalloc(S.c, (size_t)k * k * sizeof(double2));
-            double2* Tq = (double2*)dalloc(S.c, (size_t)std::max<int64_t>(m_f, n_b) * k * sizeof(double2));
+            double2* Gk = (double2*)dalloc(L.c, (size_t)k * k * sizeof(double2));
+            double2* Rk = (double2*)dalloc(L.c, (size_t)k * k * sizeof(double2));
+            double2* Tq = (double2*)dalloc(L.c, (size_t)std::max<int64_t>(m_f, n_b) * k * sizeof(double2));
             for (int pass = 0; pass < 2; ++pass) {
-                cgemm<double>(S.c, OP_H, k, k, m_f, one, Vd, m_f, 0, Vd, m_f, 0, zero, Gk, k, 0, 1, nullptr, nullptr, 0);
+                cgemm<double>(L.c, OP_H, k, k, m_f, one, Vd, m_f, 0, Vd, m_f, 0, zero, Gk, k, 0, 1, nullptr, nullptr, 0);
                 std::vector<cd> G = to_host(Gk, (size_t)k * k);
                 for (int j = 0; j < k; ++j)
                     for (int i = 0; i < j; ++i) {
@@ -821,24 +883,24 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
                 std::vector<double2> hr((size_t)k * k), hri((size_t)k * k);
                 for (size_t i = 0; i < hr.size(); ++i) { hr[i] = d2(R[i]); hri[i] = d2(Ri[i]); }
                 VSIE_CUDA(cudaMemcpy(Rk, hri.data(), hri.size() * sizeof(double2), cudaMemcpyHostToDevice));
-                cgemm<double>(S.c, OP_N, m_f, k, k, one, Vd, m_f, 0, Rk, k, 0, zero, Tq, m_f, 0, 1, nullptr, nullptr, 0);
+                cgemm<double>(L.c, OP_N, m_f, k, k, one, Vd, m_f, 0, Rk, k, 0, zero, Tq, m_f, 0, 1, nullptr, nullptr, 0);
                 VSIE_CUDA(cudaMemcpy(Vd, Tq, (size_t)m_f * k * sizeof(double2), cudaMemcpyDeviceToDevice));
                 VSIE_CUDA(cudaMemcpy(Rk, hr.data(), hr.size() * sizeof(double2), cudaMemcpyHostToDevice));
-                cgemm2<double>(S.c, OP_N, OP_H, (int)n_b, k, k, one, Up, n_b, 0, Rk, k, 0, zero, Tq, n_b, 0, 1, nullptr, nullptr, 0);
+                cgemm2<double>(L.c, OP_N, OP_H, (int)n_b, k, k, one, Up, n_b, 0, Rk, k, 0, zero, Tq, n_b, 0, 1, nullptr, nullptr, 0);
                 VSIE_CUDA(cudaMemcpy(Up, Tq, (size_t)n_b * k * sizeof(double2), cudaMemcpyDeviceToDevice));
             }
             // truncated TT-SVD of U' over (n1, n2, n3, k)
-            const double tot = frob2(S, Up, n_b * k);
+            const double tot = frob2(L, Up, n_b * k);
             const double delta2 = (tt_tol * 0.5) * (tt_tol * 0.5) * tot / 3.0;
-            Factor f1 = truncate(S, Up, nb[0], (int)((int64_t)nb[1] * nb[2] * k), delta2, 11 + a);
+            Factor f1 = truncate(L, Up, nb[0], (int)((int64_t)nb[1] * nb[2] * k), delta2, 11 + a);
             const int r1 = f1.r;
-            Factor f2 = truncate(S, f1.R, r1 * nb[1], nb[2] * k, delta2, 23 + a);
+            Factor f2 = truncate(L, f1.R, r1 * nb[1], nb[2] * k, delta2, 23 + a);
             const int r2 = f2.r;
-            Factor f3 = truncate(S, f2.R, r2 * nb[2], k, delta2, 37 + a);
+            Factor f3 = truncate(L, f2.R, r2 * nb[2], k, delta2, 37 + a);
             const int r3 = f3.r;
             // G4 = H4 Q_V^H  (r3 x m_f)
-            double2* G4 = (double2*)dalloc(S.c, (size_t)r3 * m_f * sizeof(double2));
-            cgemm2<double>(S.c, OP_N, OP_H, r3, m_f, k, one, f3.R, r3, 0, Vd, m_f, 0, zero, G4, r3, 0, 1, nullptr, nullptr, 0);
+            double2* G4 = (double2*)dalloc(L.c, (size_t)r3 * m_f * sizeof(double2));
+            cgemm2<double>(L.c, OP_N, OP_H, r3, m_f, k, one, f3.R, r3, 0, Vd, m_f, 0, zero, G4, r3, 0, 1, nullptr, nullptr, 0);
             B.tt_rank[a][0] = r1;
             B.tt_rank[a][1] = r2;
             B.tt_rank[a][2] = r3;
@@ -884,6 +946,15 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         auto& al = S.c.allocs;
         al.erase(std::remove(al.begin(), al.end(), (void*)B.dZff), al.end());
         c->allocs.push_back(B.dZff);
+    }
+    if (c->f32.ready && c->f64.ready) {
+        try {
+            build_block_precond(*c);
+        } catch (...) {
+            destroy_ctx(c);
+            throw;
+        }
+        T.mark("block preconditioner");
     }
     // ports: far ports first, then coil ports
     for (int e : mh_s.ports) {

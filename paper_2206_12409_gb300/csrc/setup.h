@@ -46,7 +46,7 @@ void efie_block(const MeshDev& ma, const MeshDev& mb, bool same, int nr, const i
                 const int* cols, double k0, double sign, double2* out, int64_t ldo);
 void coupling_block(const MeshDev& m, const GridDev& g, int nvx, const int64_t* vox, int nc,
                     const int* cols, double k0, bool near, double sign, double2* out, int64_t ldo,
-                    int64_t pstride);
+                    int64_t pstride, int only = -1);
 void field_points(const MeshDev& m, int np, const double* pts, int nc, const int* cols,
                   const double* ctr, double k0, double2* out);
 

@@ -82,6 +82,8 @@ template <typename R>
 void surface_pre(Ctx& c, int p, const cx<R>* X, int64_t ldx, cudaStream_t st) {
     OpData<R>& d = data<R>(c);
     if (c.m_n == 0 || c.nact == 0) return;
+    ProfScope ps(c, PG_PFFT, st);
+    prof_count(c, 1);
     const int64_t nrows = 3 * c.nact;
     k_scatter<R><<<nblk(nrows * p), 256, 0, st>>>(nrows, p, c.sc_ptr, c.sc_col, d.sc_val, X, ldx,
                                                   (int64_t)c.m_f, d.gc);
@@ -98,12 +100,19 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
     const int mf = c.m_f, mn = c.m_n;
     if (mn > 0) {
         const int s3 = c.s * c.s * c.s;
+        {
+        ProfScope ps(c, PG_PFFT, st);
+        prof_count(c, 1);
         k_gather<R><<<nblk((int64_t)mn * p), 256, 0, st>>>(mn, p, s3, c.nact, d.W, c.W_cidx, d.cc,
                                                            Y, ldy, (int64_t)mf);
         VSIE_CUDA(cudaGetLastError());
+        }
+        ProfScope ps(c, PG_SURF, st);
         cgemm<R>(c, OP_N, mn, p, mn, one, d.Znn, mn, 0, X + mf, ldx, 0, one, Y + mf, ldy, 0, 1,
                  nullptr, nullptr, st);
         if (c.pre_nnz > 0) {
+            ProfScope ps2(c, PG_PRECORR, st);
+            prof_count(c, 2);
             k_spmv_add<R><<<nblk(c.pre_nr * p), 256, 0, st>>>(
                 c.pre_nr, p, c.pre_rows, c.pre_ptr, c.pre_col, d.pre_val, X, ldx, (int64_t)mf, Y,
                 ldy, xb, c.mask, c.n_b, nullptr, 1);
@@ -114,6 +123,8 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
         }
     }
     if (mf > 0) {
+        {
+        ProfScope ps(c, PG_SURF, st);
         cgemm<R>(c, OP_N, mf, p, mf, one, d.Zff, mf, 0, X, ldx, 0, zero, Y, ldy, 0, 1, nullptr,
                  nullptr, st);
         if (mn > 0 && c.aca_rank > 0) {
@@ -129,7 +140,9 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
             cgemm<R>(c, OP_R, mf, p, k, one, d.V, mf, 0, d.t1, k, 0, one, Y, ldy, 0, 1, nullptr,
                      nullptr, st);
         }
+        }
         // tensor trains of the far coupling, one per component
+        ProfScope pst(c, PG_TT, st);
         const int n1 = c.nb[0], n2 = c.nb[1], n3 = c.nb[2];
         for (int a = 0; a < 3; ++a) {
             const int r1 = c.tt_rank[a][0], r2 = c.tt_rank[a][1], r3 = c.tt_rank[a][2];

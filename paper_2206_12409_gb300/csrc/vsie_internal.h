@@ -127,8 +127,21 @@ struct OpData {
     bool ready = false;
 };
 
+// Per-context profiling: kernel groups, launch counts (always), CUDA-event time
+// and algorithmic bytes (when enabled by vsie_profile).
+enum ProfGroup { PG_FFTCONV = 0, PG_PFFT = 1, PG_PRECORR = 2, PG_SURF = 3, PG_TT = 4, PG_KRYLOV = 5,
+                 PG_PRECOND = 6, PG_N = 7 };
+struct Prof {
+    bool on = false;
+    int group = PG_SURF;                       // group charged by nested launchers
+    int64_t launches[PG_N] = {0};
+    double alg_bytes[PG_N] = {0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PG_N];
+};
+
 struct Ctx {
     std::string err;
+    Prof prof;
     int device = 0;
     // problem
     int nb[3] = {0, 0, 0};      // body grid
@@ -189,6 +202,32 @@ struct Ctx {
     vsie_parts parts_view{};           // filled by vsie_get_parts
     std::vector<std::complex<double>> hZff_copy;
 };
+
+// RAII scope charging kernel launches to a profiling group.
+struct ProfScope {
+    Ctx& c;
+    int prev;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Ctx& c_, int g, cudaStream_t s, double alg_bytes = 0.0) : c(c_), prev(c_.prof.group), st(s) {
+        c.prof.group = g;
+        if (c.prof.on) {
+            cudaEventCreate(&e0);
+            cudaEventRecord(e0, st);
+            c.prof.alg_bytes[g] += alg_bytes;
+        }
+    }
+    ~ProfScope() {
+        if (c.prof.on && e0) {
+            cudaEvent_t e1;
+            cudaEventCreate(&e1);
+            cudaEventRecord(e1, st);
+            c.prof.ev[c.prof.group].push_back({e0, e1});
+        }
+        c.prof.group = prev;
+    }
+};
+inline void prof_count(Ctx& c, int n) { c.prof.launches[c.prof.group] += n; }
 
 template <typename R> OpData<R>& data(Ctx& c);
 template <> inline OpData<float>& data<float>(Ctx& c) { return c.f32; }

@@ -25,7 +25,9 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
 
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
            "vsie_matvec", "vsie_rhs_ports", "vsie_solve", "vsie_save", "vsie_load",
-           "vsie_get_parts", "vsie_destroy"]
+           "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_destroy"]
+PROFILE_GROUPS = {"fft_conv": 0, "pfft": 1, "precorrection": 2, "surface": 3, "tt": 4,
+                  "krylov": 5, "precond": 6}
 
 
 class VsieError(RuntimeError):
@@ -109,6 +111,11 @@ def load_library(path: str | None = None):
     lib.vsie_load.argtypes = [C.c_char_p, C.POINTER(P)]
     lib.vsie_get_parts.restype = C.c_int
     lib.vsie_get_parts.argtypes = [P, C.POINTER(vsie_parts)]
+    lib.vsie_profile.restype = C.c_int
+    lib.vsie_profile.argtypes = [P, C.c_int32]
+    lib.vsie_profile_query.restype = C.c_int
+    lib.vsie_profile_query.argtypes = [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_double)]
     lib.vsie_destroy.restype = None
     lib.vsie_destroy.argtypes = [P]
     _lib = lib
@@ -280,6 +287,18 @@ def vsie_get_parts(ctx):
     p = vsie_parts()
     _check(load_library().vsie_get_parts(ctx, C.byref(p)), ctx)
     return p
+
+
+def vsie_profile(ctx, enable):
+    _check(load_library().vsie_profile(ctx, int(bool(enable))), ctx)
+
+
+def vsie_profile_query(ctx, group):
+    """Returns (ms, launches, alg_bytes) of a kernel group (-1: all launches)."""
+    ms, n, b = C.c_double(), C.c_int64(), C.c_double()
+    _check(load_library().vsie_profile_query(ctx, int(group), C.byref(ms), C.byref(n), C.byref(b)),
+           ctx)
+    return ms.value, n.value, b.value
 
 
 def vsie_destroy(ctx):
