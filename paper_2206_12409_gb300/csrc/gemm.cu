@@ -127,6 +127,90 @@ __global__ void k_splitk_reduce(int M, int N, int batch, int splits, cx<R> alpha
     }
 }
 
+// Tall-skinny product C = alpha op(A) B (+ beta C) for op(A) in {N, R}, N <= NB
+// right-hand sides and large M: one thread per row of C keeps all N
+// accumulators in registers and streams its row of A (coalesced across the
+// threads of a CTA, KU loads in flight); B is staged through shared memory one
+// K-chunk at a time.  This is the shape of the dense surface blocks and of the
+// block preconditioner (M, K ~ m_f, N = p): HBM-bound on reading A once.
+template <typename R, int NB>
+__global__ void __launch_bounds__(256)
+k_gemm_ts(int conjA, int M, int N, int K, const cx<R>* __restrict__ A, int64_t lda,
+          const cx<R>* __restrict__ B, int64_t ldb, int splits, cx<R>* __restrict__ ws,
+          cx<R> alpha, cx<R> beta, cx<R>* __restrict__ C, int64_t ldc) {
+    using Cx = cx<R>;
+    constexpr int KC = 64, KU = 8;
+    __shared__ Cx Bs[KC][NB];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sp = blockIdx.y;
+    const int kper = (((K + splits - 1) / splits) + KC - 1) / KC * KC;
+    const int k0 = sp * kper, k1 = min(K, k0 + kper);
+    Cx acc[NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n) acc[n] = czero<Cx>();
+    for (int kc = k0; kc < k1; kc += KC) {
+        const int kn = min(KC, k1 - kc);
+        __syncthreads();
+        for (int e = threadIdx.x; e < KC * NB; e += blockDim.x) {
+            const int kk = e / NB, n = e - kk * NB;
+            Bs[kk][n] = (kk < kn && n < N) ? B[(size_t)(kc + kk) + (size_t)n * ldb] : czero<Cx>();
+        }
+        __syncthreads();
+        if (m < M) {
+            const Cx* Ap = A + (size_t)m + (size_t)kc * lda;
+            for (int kk0 = 0; kk0 < kn; kk0 += KU) {
+                Cx a[KU];
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    a[u] = (kk0 + u < kn) ? Ap[(size_t)(kk0 + u) * lda] : czero<Cx>();
+                    if (conjA) a[u].y = -a[u].y;
+                }
+#pragma unroll
+                for (int u = 0; u < KU; ++u)
+#pragma unroll
+                    for (int n = 0; n < NB; ++n) cfma(acc[n], a[u], Bs[kk0 + u][n]);
+            }
+        }
+    }
+    if (m >= M) return;
+    if (splits > 1) {
+        Cx* w = ws + (size_t)sp * M * N;
+#pragma unroll
+        for (int n = 0; n < NB; ++n)
+            if (n < N) w[(size_t)m + (size_t)M * n] = acc[n];
+        return;
+    }
+#pragma unroll
+    for (int n = 0; n < NB; ++n) {
+        if (n >= N) break;
+        Cx* cp = C + (size_t)m + (size_t)n * ldc;
+        Cx r = cmul(alpha, acc[n]);
+        if (beta.x != 0 || beta.y != 0) cfma(r, beta, *cp);
+        *cp = r;
+    }
+}
+
+template <typename R, int NB>
+static void launch_ts(Ctx& c, bool conjA, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+                      int64_t lda, const cx<R>* B, int64_t ldb, cx<R> beta, cx<R>* C, int64_t ldc,
+                      cudaStream_t st) {
+    OpData<R>& d = data<R>(c);
+    const int mb = (M + 255) / 256;
+    int splits = std::max(1, std::min((4 * 152 + mb - 1) / mb, K / 256));
+    while (splits > 1 && (size_t)splits * M * N > d.splitk_elems) --splits;
+    dim3 g(mb, splits);
+    prof_count(c, splits > 1 ? 2 : 1);
+    k_gemm_ts<R, NB><<<g, 256, 0, st>>>(conjA ? 1 : 0, M, N, K, A, lda, B, ldb, splits, d.splitk,
+                                        alpha, beta, C, ldc);
+    if (splits > 1) {
+        const size_t tot = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+        k_splitk_reduce<R><<<blocks, 256, 0, st>>>(M, N, 1, splits, alpha, d.splitk, beta, C, ldc,
+                                                   0, nullptr);
+    }
+    VSIE_CUDA(cudaGetLastError());
+}
+
 template <typename R, int BM, int BN, int TM, int TN>
 static void launch(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
                    int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
@@ -170,6 +254,14 @@ void cgemm2(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, co
     if (K <= 0) {
         // C = beta C
         if (beta.x == 1 && beta.y == 0) return;
+    }
+    if (batch == 1 && opB == OP_N && (opA == OP_N || opA == OP_R) && !maskB && !maskC &&
+        M >= 1024 && K >= 256 && N <= 16) {
+        if (N <= 8)
+            launch_ts<R, 8>(c, opA == OP_R, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+        else
+            launch_ts<R, 16>(c, opA == OP_R, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+        return;
     }
     if (N <= 8)
         launch<R, 128, 8, 4, 1>(c, opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
