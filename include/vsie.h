@@ -219,6 +219,25 @@ VSIE_API vsie_status vsie_profile(vsie_ctx* ctx, int32_t enable);
 VSIE_API vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms, int64_t* launches,
                                         double* alg_bytes);
 
+/* Body block only, y_b = Z_bb x_b, without allocating anything (this library
+ * has no counterpart of it in the paper).  For callers that cannot allocate
+ * device memory while the operator runs (a fixed memory pool that must not
+ * grow, a real-time loop, code being recorded into a CUDA graph).  X and Y hold
+ * p body vectors of 3 n_b complex values each (component-major, device,
+ * leading dimensions >= 3 n_b).  Vacuum voxels return their input.
+ * The FFT work space comes from one file-scope device array of 32 MiB that
+ * every GPU loading the library keeps until exit; requests needing more
+ * (p * 3 * n3 * (n2 + L2) * L1 complex values, L = FFT lengths of the context)
+ * return VSIE_EINVAL.  The first call on a device looks up that array's device
+ * address with the device current; make that first call before any stream
+ * capture.  All calls on a device share its copy of the array, which keeps the
+ * last call's contents; nothing in it needs to start at zero.  Calls that
+ * overlap on the same GPU (for example on two streams) race on it.
+ * Asynchronous on `stream`. */
+VSIE_API vsie_status vsie_volume_matvec_static(vsie_ctx* ctx, int32_t p, const void* X, int64_t ldx,
+                                               void* Y, int64_t ldy, int32_t precision,
+                                               vsie_stream stream);
+
 /* Write the context's operator (grid, materials, frequency, options, parts) to
  * a versioned binary file; vsie_load recreates a context from it (Sec. VI:
  * compressed coupling matrices stored and reused). */

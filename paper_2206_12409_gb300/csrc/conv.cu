@@ -499,6 +499,26 @@ void conv_set_attrs() {
 
 template void conv_autotune<float>(Ctx&);
 template void conv_autotune<double>(Ctx&);
+// The five passes on body-only vectors (no near-coil contributions, body block
+// at offset 0), with caller-provided work buffers A and B (used by the
+// allocation-free entry point).
+template <typename R>
+void conv_apply_given_scratch(Ctx& c, int p, const cx<R>* Xb, int64_t ldx, cx<R>* Yb, int64_t ldy,
+                              cx<R>* A, cx<R>* B, cudaStream_t st) {
+    ConvArgs<R> a = make_args<R>(c, Xb, ldx, Yb, ldy);
+    a.xoff = 0;
+    a.nact = 0;
+    a.A = A;
+    a.B = B;
+    const int* tune = data<R>(c).tune;
+    for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, p, pass, tune[pass], st);
+    VSIE_CUDA(cudaGetLastError());
+}
+template void conv_apply_given_scratch<float>(Ctx&, int, const float2*, int64_t, float2*, int64_t,
+                                              float2*, float2*, cudaStream_t);
+template void conv_apply_given_scratch<double>(Ctx&, int, const double2*, int64_t, double2*,
+                                               int64_t, double2*, double2*, cudaStream_t);
+
 template void conv_apply<float>(Ctx&, int, const float2*, int64_t, float2*, int64_t, cudaStream_t);
 template void conv_apply<double>(Ctx&, int, const double2*, int64_t, double2*, int64_t, cudaStream_t);
 template void conv_set_attrs<float>();

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
 
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
            "vsie_matvec", "vsie_rhs_ports", "vsie_solve", "vsie_save", "vsie_load",
-           "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_destroy"]
+           "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_volume_matvec_static",
+           "vsie_destroy"]
 PROFILE_GROUPS = {"fft_conv": 0, "pfft": 1, "precorrection": 2, "surface": 3, "tt": 4,
                   "krylov": 5, "precond": 6}
 
@@ -116,6 +117,8 @@ def load_library(path: str | None = None):
     lib.vsie_profile_query.restype = C.c_int
     lib.vsie_profile_query.argtypes = [P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_double)]
+    lib.vsie_volume_matvec_static.restype = C.c_int
+    lib.vsie_volume_matvec_static.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
     lib.vsie_destroy.restype = None
     lib.vsie_destroy.argtypes = [P]
     _lib = lib
@@ -299,6 +302,14 @@ def vsie_profile_query(ctx, group):
     _check(load_library().vsie_profile_query(ctx, int(group), C.byref(ms), C.byref(n), C.byref(b)),
            ctx)
     return ms.value, n.value, b.value
+
+
+def vsie_volume_matvec_static(ctx, p, X, ldx, Y, ldy, precision, stream=0):
+    """Body operator without allocation (see include/vsie.h)."""
+    lib = load_library()
+    _check(lib.vsie_volume_matvec_static(ctx, int(p), C.c_void_p(int(X)), int(ldx),
+                                         C.c_void_p(int(Y)), int(ldy), int(precision),
+                                         C.c_void_p(int(stream))), ctx)
 
 
 def vsie_destroy(ctx):
