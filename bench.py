@@ -60,17 +60,26 @@ def _conv_source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch():
-    """DRAM bytes per K1 launch group from the committed ncu summary, or None
-    when the kernel sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "fft_conv_head_traffic.json")
+def _traffic_per_launch(p):
+    """DRAM bytes per K1 launch group (p right-hand sides) from the committed ncu
+    summary, or None when the kernel sources changed since the counters were
+    taken.  The summary holds the bytes of one right-hand side; the passes move
+    data in proportion to p."""
+    path = os.path.join(ROOT, "profiles", "fft_conv_head_grid.md")
     if not os.path.exists(path):
         return None
+    vals = {}
     with open(path) as f:
-        d = json.load(f)
-    if d.get("source_hash") != _conv_source_hash():
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_hash") != _conv_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    try:
+        return float(vals["dram_bytes_per_rhs"]) * p
+    except (KeyError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -231,6 +240,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
+    torch.cuda.profiler.start()      # scope of an ncu --profile-from-start off capture
     e0.record()
     infos = []
     for _ in range(args.steps):
@@ -238,6 +248,7 @@ def main():
         infos.append((st, info))
     e1.record()
     barrier()
+    torch.cuda.profiler.stop()
     clk = clocks.stop(local)
     ms_total = e0.elapsed_time(e1)
     groups = {}
@@ -299,7 +310,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": "fft_conv (K1, 5 passes, FP32 inner operator)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_src,
-                "traffic": _traffic_per_launch(),
+                "traffic": _traffic_per_launch(p),
                 "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms}
     total_group_ms = sum(v["ms"] for v in groups.values())
     for v in groups.values():
