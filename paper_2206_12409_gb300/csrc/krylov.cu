@@ -4,14 +4,16 @@
 //
 // Both modes apply the block preconditioner of precond.cu on the right
 // (A M y = b, x = M y) unless precond = 1.
-//  mode 0 (plain FP64): GMRES(m), FP64 matvec, classical Gram-Schmidt with one
-//         re-orthogonalisation pass (CGS2), Givens rotations, true residual
-//         recomputed at every restart.
+//  mode 0 (plain FP64): GMRES(m), FP64 matvec, FP64 basis, classical
+//         Gram-Schmidt with one re-orthogonalisation pass (CGS2), Givens
+//         rotations, true residual recomputed at every restart.
 //  mode 1 (mixed): iterative refinement.  The outer loop forms the FP64
-//         residual r = b - Z x with the FP64 matvec; the inner solve is a
-//         flexible GMRES whose matvec is the FP32 operator (the FP64 basis
-//         vector is rounded to FP32, multiplied, and widened back); the
-//         orthogonalisation (CGS) and the Givens updates stay in FP64.
+//         residual r = b - Z x with the FP64 matvec; the inner solve is
+//         GMRES(m) on the FP32 operator with an FP32 basis and FP32
+//         Gram-Schmidt arithmetic (CGS), to the loose inner tolerance; its
+//         correction is widened and added to the FP64 iterate.  Dot products
+//         sum in FP32 per thread and in FP64 across threads and blocks; the
+//         Hessenberg matrix and the Givens rotations are FP64 on the host.
 // The Krylov basis is stored [i][c][n] (basis index, RHS, row), N rows each.
 // Dot products use a fixed two-stage reduction (deterministic results).
 #include "vsie_internal.h"
@@ -28,27 +30,29 @@ void matvec_internal(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64
                      cudaStream_t st);
 
 constexpr int kDotGroup = 8;     // basis vectors per dot-product group
-constexpr int kDotBlocks = 64;   // row chunks per (column, group)
+constexpr int kDotBlocks = 152;  // row chunks per (column, group): one per SM
 
-// partial[(blk * ncol + c) * nvec + i] = sum_{n in chunk} conj(V_i[c][n]) w[c][n]
+// partial[(blk * p + c) * nvec + i] = sum_{n in chunk} conj(V_i[c][n]) w[c][n]
+// (per-thread sums in R, the block tree in FP64)
+template <typename R>
 __global__ void __launch_bounds__(256)
-k_block_dot(const double2* __restrict__ V, int nvec, int64_t N, int p, const double2* __restrict__ w,
+k_block_dot(const cx<R>* __restrict__ V, int nvec, int64_t N, int p, const cx<R>* __restrict__ w,
             int64_t ldw, double2* __restrict__ partial) {
     const int c = blockIdx.y;
     const int g0 = blockIdx.z * kDotGroup;
     const int ng = min(kDotGroup, nvec - g0);
     const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
     const int64_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
-    double2 acc[kDotGroup];
+    cx<R> acc[kDotGroup];
 #pragma unroll
-    for (int g = 0; g < kDotGroup; ++g) acc[g] = make_double2(0, 0);
-    const double2* wc = w + (size_t)c * ldw;
+    for (int g = 0; g < kDotGroup; ++g) acc[g] = mk<cx<R>>(0, 0);
+    const cx<R>* wc = w + (size_t)c * ldw;
     for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-        const double2 x = wc[n];
+        const cx<R> x = wc[n];
 #pragma unroll
         for (int g = 0; g < kDotGroup; ++g) {
             if (g < ng) {
-                const double2 v = V[((size_t)(g0 + g) * p + c) * N + n];
+                const cx<R> v = V[((size_t)(g0 + g) * p + c) * N + n];
                 // conj(v) * x
                 acc[g].x += v.x * x.x + v.y * x.y;
                 acc[g].y += v.x * x.y - v.y * x.x;
@@ -57,7 +61,7 @@ k_block_dot(const double2* __restrict__ V, int nvec, int64_t N, int p, const dou
     }
     __shared__ double2 red[kDotGroup][256];
 #pragma unroll
-    for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = acc[g];
+    for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = make_double2(acc[g].x, acc[g].y);
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)
@@ -78,37 +82,43 @@ __global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int
     h[e] = s;   // h[c * nvec + i]
 }
 
-// w[c][n] += sgn * sum_i V_i[c][n] * h[c * nvec + i]
-__global__ void k_basis_update(const double2* __restrict__ V, int nvec, int64_t N, int p,
-                               const double2* __restrict__ h, double sgn, double2* __restrict__ w,
+// w[c][n] += sgn * sum_i V_i[c][n] * h[c * nvec + i]   (h in FP64, rounded to R)
+template <typename R>
+__global__ void k_basis_update(const cx<R>* __restrict__ V, int nvec, int64_t N, int p,
+                               const double2* __restrict__ h, double sgn, cx<R>* __restrict__ w,
                                int64_t ldw) {
     const int64_t tot = N * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int c = e / N;
         const int64_t n = e - (int64_t)c * N;
-        double2 s = make_double2(0, 0);
-        for (int i = 0; i < nvec; ++i) cfma(s, V[((size_t)i * p + c) * N + n], h[c * nvec + i]);
-        double2& t = w[(size_t)c * ldw + n];
-        t.x += sgn * s.x;
-        t.y += sgn * s.y;
+        cx<R> s = mk<cx<R>>(0, 0);
+        for (int i = 0; i < nvec; ++i) {
+            const double2 hv = h[c * nvec + i];
+            cfma(s, V[((size_t)i * p + c) * N + n], mk<cx<R>>((R)hv.x, (R)hv.y));
+        }
+        cx<R>& t = w[(size_t)c * ldw + n];
+        t.x += (R)sgn * s.x;
+        t.y += (R)sgn * s.y;
     }
 }
 
-// dst[c][n] = src[c][n] * scale[c]  (scale complex)
-__global__ void k_scale_cols(const double2* __restrict__ src, int64_t lds, int64_t N, int p,
-                             const double2* __restrict__ scale, double2* __restrict__ dst, int64_t ldd) {
+// dst[c][n] = src[c][n] * scale[c]  (scale complex, FP64, rounded to R)
+template <typename R>
+__global__ void k_scale_cols(const cx<R>* __restrict__ src, int64_t lds, int64_t N, int p,
+                             const double2* __restrict__ scale, cx<R>* __restrict__ dst, int64_t ldd) {
     const int64_t tot = N * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int c = e / N;
         const int64_t n = e - (int64_t)c * N;
-        dst[(size_t)c * ldd + n] = cmul(src[(size_t)c * lds + n], scale[c]);
+        dst[(size_t)c * ldd + n] = cmul(src[(size_t)c * lds + n], mk<cx<R>>((R)scale[c].x, (R)scale[c].y));
     }
 }
 
-__global__ void k_sub(const double2* __restrict__ a, int64_t lda, const double2* __restrict__ b,
-                      int64_t ldb, int64_t N, int p, double2* __restrict__ out, int64_t ldo) {
+template <typename R>
+__global__ void k_sub(const cx<R>* __restrict__ a, int64_t lda, const cx<R>* __restrict__ b,
+                      int64_t ldb, int64_t N, int p, cx<R>* __restrict__ out, int64_t ldo) {
     const int64_t tot = N * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -125,27 +135,33 @@ __global__ void k_narrow(const double2* __restrict__ a, int64_t N, int p, float2
         b[e] = make_float2((float)a[e].x, (float)a[e].y);
 }
 
-__global__ void k_widen(const float2* __restrict__ a, int64_t N, int p, double2* __restrict__ b) {
+// X[c][n] += a[c][n]  (a FP32, X FP64 with leading dimension ldx)
+__global__ void k_add_widen(const float2* __restrict__ a, int64_t N, int p, double2* __restrict__ X,
+                            int64_t ldx) {
     const int64_t tot = N * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-         e += (int64_t)gridDim.x * blockDim.x)
-        b[e] = make_double2(a[e].x, a[e].y);
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        double2& x = X[(size_t)c * ldx + n];
+        x.x += a[e].x;
+        x.y += a[e].y;
+    }
 }
 
 static int nblk(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+template <typename R>
 struct Krylov {
     Ctx& c;
     int p;
     int64_t N;
     int m;
-    double2* V;        // (m+1) x p x N
-    double2* w;        // p x N
+    cx<R>* V;          // (m+1) x p x N
+    cx<R>* w;          // p x N
     double2* h;        // p x (m+1)
     double2* part;     // kDotBlocks x p x (m+1)
     double2* scl;      // p
-    float2* x32;       // p x N
-    float2* y32;       // p x N
     cudaStream_t st;
 
     // h[c][i] = V_i^H w for i < nvec (device h), copied to host hh
@@ -153,7 +169,7 @@ struct Krylov {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 2);
         dim3 g(kDotBlocks, p, (nvec + kDotGroup - 1) / kDotGroup);
-        k_block_dot<<<g, 256, 0, st>>>(V, nvec, N, p, w, N, part);
+        k_block_dot<R><<<g, 256, 0, st>>>(V, nvec, N, p, w, N, part);
         k_reduce_dots<<<(p * nvec + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, nvec, h);
         VSIE_CUDA(cudaGetLastError());
         hh.resize((size_t)p * nvec);
@@ -166,7 +182,7 @@ struct Krylov {
         prof_count(c, 2);
         // w against itself: treat w as a one-vector basis
         dim3 g(kDotBlocks, p, 1);
-        k_block_dot<<<g, 256, 0, st>>>(w, 1, N, p, w, N, part);
+        k_block_dot<R><<<g, 256, 0, st>>>(w, 1, N, p, w, N, part);
         k_reduce_dots<<<(p + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, 1, h);
         VSIE_CUDA(cudaGetLastError());
         std::vector<double2> t(p);
@@ -175,23 +191,23 @@ struct Krylov {
         nn.resize(p);
         for (int c2 = 0; c2 < p; ++c2) nn[c2] = t[c2].x;
     }
-    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, double2* tgt,
+    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, cx<R>* tgt,
                 int64_t ld) {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(h, hh.data(), (size_t)p * nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
-        k_basis_update<<<nblk(N * p), 256, 0, st>>>(V, nvec, N, p, h, sgn, tgt, ld);
+        k_basis_update<R><<<nblk(N * p), 256, 0, st>>>(V, nvec, N, p, h, sgn, tgt, ld);
         VSIE_CUDA(cudaGetLastError());
     }
-    void scale_into(const double2* src, int64_t lds, const std::vector<std::complex<double>>& s,
-                    double2* dst, int64_t ldd) {
+    void scale_into(const cx<R>* src, int64_t lds, const std::vector<std::complex<double>>& s,
+                    cx<R>* dst, int64_t ldd) {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(scl, s.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
-        k_scale_cols<<<nblk(N * p), 256, 0, st>>>(src, lds, N, p, scl, dst, ldd);
+        k_scale_cols<R><<<nblk(N * p), 256, 0, st>>>(src, lds, N, p, scl, dst, ldd);
         VSIE_CUDA(cudaGetLastError());
     }
-    double2* basis(int i) { return V + (size_t)i * p * N; }
+    cx<R>* basis(int i) { return V + (size_t)i * p * N; }
 };
 
 using cdd = std::complex<double>;
@@ -200,17 +216,17 @@ using cdd = std::complex<double>;
 // and out) for all p columns, relative tolerance tol with respect to
 // ||r||; returns the correction in e (p x N, ld N).  iters[c] accumulates the
 // iterations until column c met its tolerance.
-template <typename Apply>
-static void gmres_core(Krylov& K, const double2* r, double tol, int maxit, bool cgs2, Apply apply,
-                       double2* e, std::vector<int>& iters, std::vector<double>& relres_est,
+template <typename R, typename Apply>
+static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool cgs2, Apply apply,
+                       cx<R>* e, std::vector<int>& iters, std::vector<double>& relres_est,
                        int& nmatvec) {
     const int p = K.p;
     const int64_t N = K.N;
     const int m = K.m;
-    VSIE_CUDA(cudaMemsetAsync(e, 0, (size_t)N * p * sizeof(double2), K.st));
+    VSIE_CUDA(cudaMemsetAsync(e, 0, (size_t)N * p * sizeof(cx<R>), K.st));
     // residual of the current correction: starts as r
-    double2* res = K.w;
-    VSIE_CUDA(cudaMemcpyAsync(res, r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, K.st));
+    cx<R>* res = K.w;
+    VSIE_CUDA(cudaMemcpyAsync(res, r, (size_t)N * p * sizeof(cx<R>), cudaMemcpyDeviceToDevice, K.st));
     std::vector<double> nr0;
     K.norms(nr0);
     std::vector<double> beta0(p);
@@ -310,7 +326,7 @@ static void gmres_core(Krylov& K, const double2* r, double tol, int maxit, bool 
         // true residual of the correction: res = r - A e
         apply(e, K.w);
         ++nmatvec;
-        k_sub<<<nblk(N * p), 256, 0, K.st>>>(r, N, K.w, N, N, p, K.w, N);
+        k_sub<R><<<nblk(N * p), 256, 0, K.st>>>(r, N, K.w, N, N, p, K.w, N);
         VSIE_CUDA(cudaGetLastError());
         for (int c = 0; c < p; ++c) done[c] = done[c] || cyc_done[c];
         // (loop re-evaluates the true residual norms at the top)
@@ -319,12 +335,6 @@ static void gmres_core(Krylov& K, const double2* r, double tol, int maxit, bool 
     K.norms(nr);
     for (int c = 0; c < p; ++c) relres_est[c] = beta0[c] > 0 ? std::sqrt(nr[c]) / beta0[c] : 0.0;
 }
-
-struct SolveWork {
-    double2 *V = nullptr, *w = nullptr, *h = nullptr, *part = nullptr, *scl = nullptr;
-    double2 *r = nullptr, *e = nullptr, *Ax = nullptr, *z = nullptr;
-    float2 *x32 = nullptr, *y32 = nullptr, *t32 = nullptr;
-};
 
 vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X, int64_t ldx,
                        double tol, const vsie_solve_opts* o_in, vsie_solve_info* info,
@@ -342,11 +352,13 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     if (o.mode == 1 && !c.f32.ready) throw Error(VSIE_EUNSUPPORTED, "mode 1 needs the C64 operator");
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t N = c.N;
-    // workspace (kept in the context between solves)
+    const size_t pN = (size_t)p * N;
+    // workspace (kept in the context between solves): the basis in the
+    // precision of the mode, four FP64 and five FP32 p x N blocks, dot scratch
     const bool use_pc = o.precond != 1;
     if (use_pc) build_block_precond(c);
-    const size_t need = ((size_t)(m + 1) * p * N + 5 * (size_t)p * N) * sizeof(double2) +
-                        3 * (size_t)p * N * sizeof(float2) +
+    const size_t basis_bytes = (size_t)(m + 1) * pN * (o.mode == 0 ? sizeof(double2) : sizeof(float2));
+    const size_t need = basis_bytes + 5 * pN * sizeof(double2) + 5 * pN * sizeof(float2) +
                         ((size_t)kDotBlocks * p * (m + 1) + (size_t)p * (m + 1) + p) * sizeof(double2) +
                         16 * 256;   // slack for the 256-byte alignment of each slice below
     if (c.kr_bytes < need) {
@@ -360,31 +372,33 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
         c.kr_V = (double2*)dalloc(c, need);
         c.kr_bytes = need;
     }
-    SolveWork W;
     char* base = (char*)c.kr_V;
     auto take = [&](size_t bytes) { char* q = base; base += (bytes + 255) / 256 * 256; return q; };
-    W.V = (double2*)take((size_t)(m + 1) * p * N * sizeof(double2));
-    W.w = (double2*)take((size_t)p * N * sizeof(double2));
-    W.r = (double2*)take((size_t)p * N * sizeof(double2));
-    W.e = (double2*)take((size_t)p * N * sizeof(double2));
-    W.Ax = (double2*)take((size_t)p * N * sizeof(double2));
-    W.z = (double2*)take((size_t)p * N * sizeof(double2));
-    W.x32 = (float2*)take((size_t)p * N * sizeof(float2));
-    W.y32 = (float2*)take((size_t)p * N * sizeof(float2));
-    W.t32 = (float2*)take((size_t)p * N * sizeof(float2));
-    W.part = (double2*)take((size_t)kDotBlocks * p * (m + 1) * sizeof(double2));
-    W.h = (double2*)take((size_t)p * (m + 1) * sizeof(double2));
-    W.scl = (double2*)take((size_t)p * sizeof(double2));
-    Krylov K{c, p, N, m, W.V, W.w, W.h, W.part, W.scl, W.x32, W.y32, st};
+    void* Vb = take(basis_bytes);
+    double2* w64 = (double2*)take(pN * sizeof(double2));
+    double2* r64 = (double2*)take(pN * sizeof(double2));
+    double2* e64 = (double2*)take(pN * sizeof(double2));
+    double2* Ax = (double2*)take(pN * sizeof(double2));
+    double2* z64 = (double2*)take(pN * sizeof(double2));
+    float2* w32 = (float2*)take(pN * sizeof(float2));
+    float2* r32 = (float2*)take(pN * sizeof(float2));
+    float2* e32 = (float2*)take(pN * sizeof(float2));
+    float2* t32 = (float2*)take(pN * sizeof(float2));
+    float2* z32 = (float2*)take(pN * sizeof(float2));
+    double2* part = (double2*)take((size_t)kDotBlocks * p * (m + 1) * sizeof(double2));
+    double2* hbuf = (double2*)take((size_t)p * (m + 1) * sizeof(double2));
+    double2* scl = (double2*)take((size_t)p * sizeof(double2));
+    Krylov<double> K64{c, p, N, m, o.mode == 0 ? (double2*)Vb : nullptr, w64, hbuf, part, scl, st};
+    Krylov<float> K32{c, p, N, m, o.mode == 0 ? nullptr : (float2*)Vb, w32, hbuf, part, scl, st};
     int mv64 = 0, mv32 = 0, outer = 0;
     std::vector<int> iters(p, 0);
     std::vector<double> est;
     // ||b|| per column
-    VSIE_CUDA(cudaMemcpy2DAsync(W.r, N * sizeof(double2), B, ldb * sizeof(double2),
+    VSIE_CUDA(cudaMemcpy2DAsync(r64, N * sizeof(double2), B, ldb * sizeof(double2),
                                 N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
-    VSIE_CUDA(cudaMemcpyAsync(W.w, W.r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    VSIE_CUDA(cudaMemcpyAsync(w64, r64, pN * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     std::vector<double> bn2;
-    K.norms(bn2);
+    K64.norms(bn2);
     std::vector<double> bn(p);
     for (int q = 0; q < p; ++q) {
         bn[q] = std::sqrt(bn2[q]);
@@ -393,63 +407,47 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     auto apply64 = [&](const double2* in, double2* out) {
         matvec_internal<double>(c, p, in, N, out, N, st);
     };
-    // right-preconditioned operators A M (FP64) and A32 M32 (FP32 inside)
+    // right-preconditioned operators A M (FP64) and A32 M32 (FP32)
     auto apply64_pc = [&](const double2* in, double2* out) {
         if (!use_pc) { apply64(in, out); return; }
-        apply_block_precond<double>(c, p, in, N, W.z, N, st);
-        apply64(W.z, out);
+        apply_block_precond<double>(c, p, in, N, z64, N, st);
+        apply64(z64, out);
     };
-    auto apply32_pc = [&](const double2* in, double2* out) {
-        k_narrow<<<nblk(N * p), 256, 0, st>>>(in, N, p, W.x32);
-        const float2* src = W.x32;
+    auto apply32_pc = [&](const float2* in, float2* out) {
+        const float2* src = in;
         if (use_pc) {
-            apply_block_precond<float>(c, p, W.x32, N, W.t32, N, st);
-            src = W.t32;
+            apply_block_precond<float>(c, p, in, N, t32, N, st);
+            src = t32;
         }
-        matvec_internal<float>(c, p, src, N, W.y32, N, st);
-        k_widen<<<nblk(N * p), 256, 0, st>>>(W.y32, N, p, out);
-        VSIE_CUDA(cudaGetLastError());
-    };
-    // x-space correction M e (FP64 path) and M32 e (refinement path)
-    auto precond64 = [&](const double2* in, double2* out) {
-        if (!use_pc) {
-            VSIE_CUDA(cudaMemcpyAsync(out, in, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            return;
-        }
-        apply_block_precond<double>(c, p, in, N, out, N, st);
-    };
-    auto precond32 = [&](const double2* in, double2* out) {
-        if (!use_pc) {
-            VSIE_CUDA(cudaMemcpyAsync(out, in, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            return;
-        }
-        k_narrow<<<nblk(N * p), 256, 0, st>>>(in, N, p, W.x32);
-        apply_block_precond<float>(c, p, W.x32, N, W.t32, N, st);
-        k_widen<<<nblk(N * p), 256, 0, st>>>(W.t32, N, p, out);
-        VSIE_CUDA(cudaGetLastError());
+        matvec_internal<float>(c, p, src, N, out, N, st);
     };
     // x = 0
     VSIE_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, N * sizeof(double2), p, st));
     std::vector<double> relres(p, 1.0);
     if (o.mode == 0) {
         int cnt = 0;
-        gmres_core(K, W.r, tol, maxit, true, apply64_pc, W.e, iters, est, cnt);
+        gmres_core(K64, r64, tol, maxit, true, apply64_pc, e64, iters, est, cnt);
         mv64 += cnt;
-        precond64(W.e, W.z);
-        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), W.z, N * sizeof(double2),
+        // x = M e
+        const double2* xs = e64;
+        if (use_pc) {
+            apply_block_precond<double>(c, p, e64, N, z64, N, st);
+            xs = z64;
+        }
+        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), xs, N * sizeof(double2),
                                     N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     } else {
         for (outer = 0; outer < max_outer; ++outer) {
             // r = b - Z64 x
-            VSIE_CUDA(cudaMemcpy2DAsync(W.e, N * sizeof(double2), X, ldx * sizeof(double2),
+            VSIE_CUDA(cudaMemcpy2DAsync(e64, N * sizeof(double2), X, ldx * sizeof(double2),
                                         N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
-            apply64(W.e, W.Ax);
+            apply64(e64, Ax);
             ++mv64;
-            k_sub<<<nblk(N * p), 256, 0, st>>>(B, ldb, W.Ax, N, N, p, W.r, N);
+            k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, N, N, p, r64, N);
             VSIE_CUDA(cudaGetLastError());
-            VSIE_CUDA(cudaMemcpyAsync(W.w, W.r, (size_t)N * p * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            VSIE_CUDA(cudaMemcpyAsync(w64, r64, pN * sizeof(double2), cudaMemcpyDeviceToDevice, st));
             std::vector<double> rn2;
-            K.norms(rn2);
+            K64.norms(rn2);
             bool conv = true;
             for (int q = 0; q < p; ++q) {
                 relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
@@ -467,25 +465,29 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             int budget = maxit;
             for (int q = 0; q < p; ++q) budget = std::min(budget, maxit - iters[q]);
             if (budget <= 0) break;
-            gmres_core(K, W.r, itol, budget, false, apply32_pc, W.e, iters, est, cnt);
+            k_narrow<<<nblk(N * p), 256, 0, st>>>(r64, N, p, r32);
+            VSIE_CUDA(cudaGetLastError());
+            gmres_core(K32, r32, itol, budget, false, apply32_pc, e32, iters, est, cnt);
             mv32 += cnt;
-            // x += M e
-            precond32(W.e, W.z);
-            std::vector<cdd> onev((size_t)p, 1.0);
-            VSIE_CUDA(cudaMemcpyAsync(W.h, onev.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
-            k_basis_update<<<nblk(N * p), 256, 0, st>>>(W.z, 1, N, p, W.h, 1.0, X, ldx);
+            // x += M32 e
+            const float2* corr = e32;
+            if (use_pc) {
+                apply_block_precond<float>(c, p, e32, N, z32, N, st);
+                corr = z32;
+            }
+            k_add_widen<<<nblk(N * p), 256, 0, st>>>(corr, N, p, X, ldx);
             VSIE_CUDA(cudaGetLastError());
         }
     }
     // final true FP64 residual
-    VSIE_CUDA(cudaMemcpy2DAsync(W.e, N * sizeof(double2), X, ldx * sizeof(double2),
+    VSIE_CUDA(cudaMemcpy2DAsync(e64, N * sizeof(double2), X, ldx * sizeof(double2),
                                 N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
-    apply64(W.e, W.Ax);
+    apply64(e64, Ax);
     ++mv64;
-    k_sub<<<nblk(N * p), 256, 0, st>>>(B, ldb, W.Ax, N, N, p, W.w, N);
+    k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, N, N, p, w64, N);
     VSIE_CUDA(cudaGetLastError());
     std::vector<double> rn2;
-    K.norms(rn2);
+    K64.norms(rn2);
     bool conv = true;
     for (int q = 0; q < p; ++q) {
         relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
