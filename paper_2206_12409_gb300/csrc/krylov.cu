@@ -32,45 +32,98 @@ void matvec_internal(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64
 constexpr int kDotGroup = 8;     // basis vectors per dot-product group
 constexpr int kDotBlocks = 152;  // row chunks per (column, group): one per SM
 
+// Vector loads of the FP32 kernels move two complex values (one float4); the
+// FP64 kernels one (double2).  Every p x N block below has a leading dimension
+// ld >= N; the FP32 paths need ld even (16-byte aligned rows).
+template <typename R> struct Pack;
+template <> struct Pack<float> { using T = float4; static constexpr int K = 2; };
+template <> struct Pack<double> { using T = double2; static constexpr int K = 1; };
+
+// conj(v) . x summed over the complex values of one pack, accumulated into a
+template <typename T, typename A>
+__device__ __forceinline__ void pack_dot(A& a, const T& v, const T& x);
+template <>
+__device__ __forceinline__ void pack_dot<float4, float2>(float2& a, const float4& v, const float4& x) {
+    a.x += v.x * x.x + v.y * x.y + v.z * x.z + v.w * x.w;
+    a.y += v.x * x.y - v.y * x.x + v.z * x.w - v.w * x.z;
+}
+template <>
+__device__ __forceinline__ void pack_dot<double2, double2>(double2& a, const double2& v, const double2& x) {
+    a.x += v.x * x.x + v.y * x.y;
+    a.y += v.x * x.y - v.y * x.x;
+}
+// s += v * h for each complex value of the pack
+__device__ __forceinline__ void pack_fma(float4& s, const float4& v, float2 h) {
+    s.x += v.x * h.x - v.y * h.y;
+    s.y += v.x * h.y + v.y * h.x;
+    s.z += v.z * h.x - v.w * h.y;
+    s.w += v.z * h.y + v.w * h.x;
+}
+__device__ __forceinline__ void pack_fma(double2& s, const double2& v, double2 h) {
+    s.x += v.x * h.x - v.y * h.y;
+    s.y += v.x * h.y + v.y * h.x;
+}
+__device__ __forceinline__ void pack_sub(float4& t, const float4& s, float sg) {
+    t.x += sg * s.x; t.y += sg * s.y; t.z += sg * s.z; t.w += sg * s.w;
+}
+__device__ __forceinline__ void pack_sub(double2& t, const double2& s, double sg) {
+    t.x += sg * s.x; t.y += sg * s.y;
+}
+
 // partial[(blk * p + c) * nvec + i] = sum_{n in chunk} conj(V_i[c][n]) w[c][n]
-// (per-thread sums in R, the block tree in FP64)
+// V_i[c] = V + (i p + c) ld.  Per-thread sums in R, the warp and block sums in
+// FP64.  Chunks are whole packs; block 0 adds the odd last row.
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_block_dot(const cx<R>* __restrict__ V, int nvec, int64_t N, int p, const cx<R>* __restrict__ w,
-            int64_t ldw, double2* __restrict__ partial) {
+k_block_dot(const cx<R>* __restrict__ V, int nvec, int64_t N, int64_t ld, int p,
+            const cx<R>* __restrict__ w, int64_t ldw, double2* __restrict__ partial) {
+    using T = typename Pack<R>::T;
+    constexpr int PK = Pack<R>::K;
     const int c = blockIdx.y;
     const int g0 = blockIdx.z * kDotGroup;
     const int ng = min(kDotGroup, nvec - g0);
-    const int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
-    const int64_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    const int64_t NP = N / PK;
+    const int64_t chunk = (NP + gridDim.x - 1) / gridDim.x;
+    const int64_t n0 = blockIdx.x * chunk, n1 = min(NP, n0 + chunk);
     cx<R> acc[kDotGroup];
 #pragma unroll
     for (int g = 0; g < kDotGroup; ++g) acc[g] = mk<cx<R>>(0, 0);
-    const cx<R>* wc = w + (size_t)c * ldw;
+    const T* wc = reinterpret_cast<const T*>(w + (size_t)c * ldw);
     for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-        const cx<R> x = wc[n];
+        const T x = wc[n];
+        T v[kDotGroup];
 #pragma unroll
-        for (int g = 0; g < kDotGroup; ++g) {
-            if (g < ng) {
-                const cx<R> v = V[((size_t)(g0 + g) * p + c) * N + n];
-                // conj(v) * x
-                acc[g].x += v.x * x.x + v.y * x.y;
-                acc[g].y += v.x * x.y - v.y * x.x;
-            }
+        for (int g = 0; g < kDotGroup; ++g)
+            if (g < ng) v[g] = reinterpret_cast<const T*>(V + ((size_t)(g0 + g) * p + c) * ld)[n];
+#pragma unroll
+        for (int g = 0; g < kDotGroup; ++g)
+            if (g < ng) pack_dot(acc[g], v[g], x);
+    }
+    if (PK == 2 && (N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const cx<R> x = w[(size_t)c * ldw + N - 1];
+        for (int g = 0; g < ng; ++g) {
+            const cx<R> v = V[((size_t)(g0 + g) * p + c) * ld + N - 1];
+            acc[g].x += v.x * x.x + v.y * x.y;
+            acc[g].y += v.x * x.y - v.y * x.x;
         }
     }
-    __shared__ double2 red[kDotGroup][256];
+    __shared__ double2 red[kDotGroup][8];
 #pragma unroll
-    for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = make_double2(acc[g].x, acc[g].y);
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
+    for (int g = 0; g < kDotGroup; ++g) {
+        double rx = acc[g].x, ry = acc[g].y;
 #pragma unroll
-            for (int g = 0; g < kDotGroup; ++g) red[g][threadIdx.x] = cadd(red[g][threadIdx.x], red[g][threadIdx.x + s]);
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) {
+            rx += __shfl_down_sync(0xffffffffu, rx, o);
+            ry += __shfl_down_sync(0xffffffffu, ry, o);
+        }
+        if ((threadIdx.x & 31) == 0) red[g][threadIdx.x >> 5] = make_double2(rx, ry);
     }
-    if (threadIdx.x < ng)
-        partial[((size_t)blockIdx.x * p + c) * nvec + g0 + threadIdx.x] = red[threadIdx.x][0];
+    __syncthreads();
+    if (threadIdx.x < ng) {
+        double2 s = make_double2(0, 0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s = cadd(s, red[threadIdx.x][q]);
+        partial[((size_t)blockIdx.x * p + c) * nvec + g0 + threadIdx.x] = s;
+    }
 }
 
 __global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int p, int nvec,
@@ -83,21 +136,44 @@ __global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int
 }
 
 // w[c][n] += sgn * sum_i V_i[c][n] * h[c * nvec + i]   (h in FP64, rounded to R)
+// grid (blocks, p); dynamic shared memory: nvec complex values of R
 template <typename R>
-__global__ void k_basis_update(const cx<R>* __restrict__ V, int nvec, int64_t N, int p,
-                               const double2* __restrict__ h, double sgn, cx<R>* __restrict__ w,
-                               int64_t ldw) {
-    const int64_t tot = N * p;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = e / N;
-        const int64_t n = e - (int64_t)c * N;
-        cx<R> s = mk<cx<R>>(0, 0);
-        for (int i = 0; i < nvec; ++i) {
-            const double2 hv = h[c * nvec + i];
-            cfma(s, V[((size_t)i * p + c) * N + n], mk<cx<R>>((R)hv.x, (R)hv.y));
+__global__ void __launch_bounds__(256)
+k_basis_update(const cx<R>* __restrict__ V, int nvec, int64_t N, int64_t ld, int p,
+               const double2* __restrict__ h, double sgn, cx<R>* __restrict__ w, int64_t ldw) {
+    using T = typename Pack<R>::T;
+    constexpr int PK = Pack<R>::K;
+    extern __shared__ __align__(16) unsigned char kb_smem[];
+    cx<R>* hs = reinterpret_cast<cx<R>*>(kb_smem);
+    const int c = blockIdx.y;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+        hs[i] = mk<cx<R>>((R)h[c * nvec + i].x, (R)h[c * nvec + i].y);
+    __syncthreads();
+    const int64_t NP = N / PK;
+    T* wc = reinterpret_cast<T*>(w + (size_t)c * ldw);
+    const T* Vc = reinterpret_cast<const T*>(V + (size_t)c * ld);
+    const size_t vstride = (size_t)p * ld / PK;   // packs between basis vectors
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < NP;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        T s;
+        memset(&s, 0, sizeof(T));
+        int i = 0;
+        for (; i + 8 <= nvec; i += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = Vc[(size_t)(i + u) * vstride + n];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) pack_fma(s, v[u], hs[i + u]);
         }
-        cx<R>& t = w[(size_t)c * ldw + n];
+        for (; i < nvec; ++i) pack_fma(s, Vc[(size_t)i * vstride + n], hs[i]);
+        T t = wc[n];
+        pack_sub(t, s, (R)sgn);
+        wc[n] = t;
+    }
+    if (PK == 2 && (N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        cx<R> s = mk<cx<R>>(0, 0);
+        for (int i = 0; i < nvec; ++i) cfma(s, V[((size_t)i * p + c) * ld + N - 1], hs[i]);
+        cx<R>& t = w[(size_t)c * ldw + N - 1];
         t.x += (R)sgn * s.x;
         t.y += (R)sgn * s.y;
     }
@@ -128,24 +204,30 @@ __global__ void k_sub(const cx<R>* __restrict__ a, int64_t lda, const cx<R>* __r
     }
 }
 
-__global__ void k_narrow(const double2* __restrict__ a, int64_t N, int p, float2* __restrict__ b) {
-    const int64_t tot = N * p;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-         e += (int64_t)gridDim.x * blockDim.x)
-        b[e] = make_float2((float)a[e].x, (float)a[e].y);
-}
-
-// X[c][n] += a[c][n]  (a FP32, X FP64 with leading dimension ldx)
-__global__ void k_add_widen(const float2* __restrict__ a, int64_t N, int p, double2* __restrict__ X,
-                            int64_t ldx) {
+__global__ void k_narrow(const double2* __restrict__ a, int64_t lda, int64_t N, int p,
+                         float2* __restrict__ b, int64_t ldb) {
     const int64_t tot = N * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int c = e / N;
         const int64_t n = e - (int64_t)c * N;
+        const double2 v = a[(size_t)c * lda + n];
+        b[(size_t)c * ldb + n] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// X[c][n] += a[c][n]  (a FP32, X FP64)
+__global__ void k_add_widen(const float2* __restrict__ a, int64_t lda, int64_t N, int p,
+                            double2* __restrict__ X, int64_t ldx) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        const float2 v = a[(size_t)c * lda + n];
         double2& x = X[(size_t)c * ldx + n];
-        x.x += a[e].x;
-        x.y += a[e].y;
+        x.x += v.x;
+        x.y += v.y;
     }
 }
 
@@ -156,9 +238,10 @@ struct Krylov {
     Ctx& c;
     int p;
     int64_t N;
+    int64_t ld;        // leading dimension of every p x N block (even)
     int m;
-    cx<R>* V;          // (m+1) x p x N
-    cx<R>* w;          // p x N
+    cx<R>* V;          // (m+1) x p x ld
+    cx<R>* w;          // p x ld
     double2* h;        // p x (m+1)
     double2* part;     // kDotBlocks x p x (m+1)
     double2* scl;      // p
@@ -169,7 +252,7 @@ struct Krylov {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 2);
         dim3 g(kDotBlocks, p, (nvec + kDotGroup - 1) / kDotGroup);
-        k_block_dot<R><<<g, 256, 0, st>>>(V, nvec, N, p, w, N, part);
+        k_block_dot<R><<<g, 256, 0, st>>>(V, nvec, N, ld, p, w, ld, part);
         k_reduce_dots<<<(p * nvec + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, nvec, h);
         VSIE_CUDA(cudaGetLastError());
         hh.resize((size_t)p * nvec);
@@ -182,7 +265,7 @@ struct Krylov {
         prof_count(c, 2);
         // w against itself: treat w as a one-vector basis
         dim3 g(kDotBlocks, p, 1);
-        k_block_dot<R><<<g, 256, 0, st>>>(w, 1, N, p, w, N, part);
+        k_block_dot<R><<<g, 256, 0, st>>>(w, 1, N, ld, p, w, ld, part);
         k_reduce_dots<<<(p + 255) / 256, 256, 0, st>>>(part, kDotBlocks, p, 1, h);
         VSIE_CUDA(cudaGetLastError());
         std::vector<double2> t(p);
@@ -191,42 +274,44 @@ struct Krylov {
         nn.resize(p);
         for (int c2 = 0; c2 < p; ++c2) nn[c2] = t[c2].x;
     }
-    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, cx<R>* tgt,
-                int64_t ld) {
+    // tgt (p x N, leading dimension ld) += sgn V hh
+    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, cx<R>* tgt) {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(h, hh.data(), (size_t)p * nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
-        k_basis_update<R><<<nblk(N * p), 256, 0, st>>>(V, nvec, N, p, h, sgn, tgt, ld);
+        const int64_t packs = N / Pack<R>::K;
+        const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((packs + 255) / 256, 1216));
+        k_basis_update<R><<<dim3(bx, p), 256, (size_t)nvec * sizeof(cx<R>), st>>>(V, nvec, N, ld, p, h,
+                                                                                 sgn, tgt, ld);
         VSIE_CUDA(cudaGetLastError());
     }
-    void scale_into(const cx<R>* src, int64_t lds, const std::vector<std::complex<double>>& s,
-                    cx<R>* dst, int64_t ldd) {
+    void scale_into(const cx<R>* src, const std::vector<std::complex<double>>& s, cx<R>* dst) {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(scl, s.data(), p * sizeof(double2), cudaMemcpyHostToDevice, st));
-        k_scale_cols<R><<<nblk(N * p), 256, 0, st>>>(src, lds, N, p, scl, dst, ldd);
+        k_scale_cols<R><<<nblk(N * p), 256, 0, st>>>(src, ld, N, p, scl, dst, ld);
         VSIE_CUDA(cudaGetLastError());
     }
-    cx<R>* basis(int i) { return V + (size_t)i * p * N; }
+    cx<R>* basis(int i) { return V + (size_t)i * p * ld; }
 };
 
 using cdd = std::complex<double>;
 
 // One restarted GMRES(m) solve of A e = r (A applied through `apply`, FP64 in
 // and out) for all p columns, relative tolerance tol with respect to
-// ||r||; returns the correction in e (p x N, ld N).  iters[c] accumulates the
+// ||r||; returns the correction in e (p x N, leading dimension K.ld).  iters[c] accumulates the
 // iterations until column c met its tolerance.
 template <typename R, typename Apply>
 static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool cgs2, Apply apply,
                        cx<R>* e, std::vector<int>& iters, std::vector<double>& relres_est,
                        int& nmatvec) {
     const int p = K.p;
-    const int64_t N = K.N;
+    const int64_t N = K.N, ld = K.ld;
     const int m = K.m;
-    VSIE_CUDA(cudaMemsetAsync(e, 0, (size_t)N * p * sizeof(cx<R>), K.st));
+    VSIE_CUDA(cudaMemsetAsync(e, 0, (size_t)ld * p * sizeof(cx<R>), K.st));
     // residual of the current correction: starts as r
     cx<R>* res = K.w;
-    VSIE_CUDA(cudaMemcpyAsync(res, r, (size_t)N * p * sizeof(cx<R>), cudaMemcpyDeviceToDevice, K.st));
+    VSIE_CUDA(cudaMemcpyAsync(res, r, (size_t)ld * p * sizeof(cx<R>), cudaMemcpyDeviceToDevice, K.st));
     std::vector<double> nr0;
     K.norms(nr0);
     std::vector<double> beta0(p);
@@ -253,7 +338,7 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
         // v0 = res / beta
         std::vector<cdd> sc(p);
         for (int c = 0; c < p; ++c) sc[c] = beta[c] > 0 ? 1.0 / beta[c] : 0.0;
-        K.scale_into(res, N, sc, K.basis(0), N);
+        K.scale_into(res, sc, K.basis(0));
         std::vector<std::vector<cdd>> H(p, std::vector<cdd>((size_t)(m + 1) * m, 0.0));
         std::vector<std::vector<cdd>> cs(p, std::vector<cdd>(m)), sn(p, std::vector<cdd>(m));
         std::vector<std::vector<cdd>> g(p, std::vector<cdd>(m + 1, 0.0));
@@ -265,10 +350,10 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
             ++nmatvec;
             std::vector<cdd> hh, hh2;
             K.dots(j + 1, hh);
-            K.update(j + 1, hh, -1.0, K.w, N);
+            K.update(j + 1, hh, -1.0, K.w);
             if (cgs2) {
                 K.dots(j + 1, hh2);
-                K.update(j + 1, hh2, -1.0, K.w, N);
+                K.update(j + 1, hh2, -1.0, K.w);
                 for (size_t q = 0; q < hh.size(); ++q) hh[q] += hh2[q];
             }
             std::vector<double> nw;
@@ -307,7 +392,7 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
             }
             bool all2 = true;
             for (int c = 0; c < p; ++c) all2 = all2 && cyc_done[c];
-            if (j + 1 < m) K.scale_into(K.w, N, inv, K.basis(j + 1), N);
+            if (j + 1 < m) K.scale_into(K.w, inv, K.basis(j + 1));
             if (all2) { ++j; break; }
         }
         // y = H^-1 g (upper triangular, k = j columns); e += V y
@@ -322,11 +407,11 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
                 Y[(size_t)c * k + i] = d != 0.0 ? s / d : 0.0;
             }
         }
-        K.update(k, Y, 1.0, e, N);
+        K.update(k, Y, 1.0, e);
         // true residual of the correction: res = r - A e
         apply(e, K.w);
         ++nmatvec;
-        k_sub<R><<<nblk(N * p), 256, 0, K.st>>>(r, N, K.w, N, N, p, K.w, N);
+        k_sub<R><<<nblk(N * p), 256, 0, K.st>>>(r, ld, K.w, ld, N, p, K.w, ld);
         VSIE_CUDA(cudaGetLastError());
         for (int c = 0; c < p; ++c) done[c] = done[c] || cyc_done[c];
         // (loop re-evaluates the true residual norms at the top)
@@ -352,7 +437,8 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     if (o.mode == 1 && !c.f32.ready) throw Error(VSIE_EUNSUPPORTED, "mode 1 needs the C64 operator");
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t N = c.N;
-    const size_t pN = (size_t)p * N;
+    const int64_t L = (N + 63) / 64 * 64;   // padded leading dimension of the work blocks
+    const size_t pN = (size_t)p * L;
     // workspace (kept in the context between solves): the basis in the
     // precision of the mode, four FP64 and five FP32 p x N blocks, dot scratch
     const bool use_pc = o.precond != 1;
@@ -388,13 +474,13 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     double2* part = (double2*)take((size_t)kDotBlocks * p * (m + 1) * sizeof(double2));
     double2* hbuf = (double2*)take((size_t)p * (m + 1) * sizeof(double2));
     double2* scl = (double2*)take((size_t)p * sizeof(double2));
-    Krylov<double> K64{c, p, N, m, o.mode == 0 ? (double2*)Vb : nullptr, w64, hbuf, part, scl, st};
-    Krylov<float> K32{c, p, N, m, o.mode == 0 ? nullptr : (float2*)Vb, w32, hbuf, part, scl, st};
+    Krylov<double> K64{c, p, N, L, m, o.mode == 0 ? (double2*)Vb : nullptr, w64, hbuf, part, scl, st};
+    Krylov<float> K32{c, p, N, L, m, o.mode == 0 ? nullptr : (float2*)Vb, w32, hbuf, part, scl, st};
     int mv64 = 0, mv32 = 0, outer = 0;
     std::vector<int> iters(p, 0);
     std::vector<double> est;
     // ||b|| per column
-    VSIE_CUDA(cudaMemcpy2DAsync(r64, N * sizeof(double2), B, ldb * sizeof(double2),
+    VSIE_CUDA(cudaMemcpy2DAsync(r64, L * sizeof(double2), B, ldb * sizeof(double2),
                                 N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     VSIE_CUDA(cudaMemcpyAsync(w64, r64, pN * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     std::vector<double> bn2;
@@ -405,21 +491,21 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
         if (!std::isfinite(bn[q])) throw Error(VSIE_EBREAKDOWN, "non-finite right-hand side");
     }
     auto apply64 = [&](const double2* in, double2* out) {
-        matvec_internal<double>(c, p, in, N, out, N, st);
+        matvec_internal<double>(c, p, in, L, out, L, st);
     };
     // right-preconditioned operators A M (FP64) and A32 M32 (FP32)
     auto apply64_pc = [&](const double2* in, double2* out) {
         if (!use_pc) { apply64(in, out); return; }
-        apply_block_precond<double>(c, p, in, N, z64, N, st);
+        apply_block_precond<double>(c, p, in, L, z64, L, st);
         apply64(z64, out);
     };
     auto apply32_pc = [&](const float2* in, float2* out) {
         const float2* src = in;
         if (use_pc) {
-            apply_block_precond<float>(c, p, in, N, t32, N, st);
+            apply_block_precond<float>(c, p, in, L, t32, L, st);
             src = t32;
         }
-        matvec_internal<float>(c, p, src, N, out, N, st);
+        matvec_internal<float>(c, p, src, L, out, L, st);
     };
     // x = 0
     VSIE_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, N * sizeof(double2), p, st));
@@ -431,19 +517,19 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
         // x = M e
         const double2* xs = e64;
         if (use_pc) {
-            apply_block_precond<double>(c, p, e64, N, z64, N, st);
+            apply_block_precond<double>(c, p, e64, L, z64, L, st);
             xs = z64;
         }
-        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), xs, N * sizeof(double2),
+        VSIE_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double2), xs, L * sizeof(double2),
                                     N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     } else {
         for (outer = 0; outer < max_outer; ++outer) {
             // r = b - Z64 x
-            VSIE_CUDA(cudaMemcpy2DAsync(e64, N * sizeof(double2), X, ldx * sizeof(double2),
+            VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
                                         N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
             apply64(e64, Ax);
             ++mv64;
-            k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, N, N, p, r64, N);
+            k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, r64, L);
             VSIE_CUDA(cudaGetLastError());
             VSIE_CUDA(cudaMemcpyAsync(w64, r64, pN * sizeof(double2), cudaMemcpyDeviceToDevice, st));
             std::vector<double> rn2;
@@ -465,26 +551,26 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             int budget = maxit;
             for (int q = 0; q < p; ++q) budget = std::min(budget, maxit - iters[q]);
             if (budget <= 0) break;
-            k_narrow<<<nblk(N * p), 256, 0, st>>>(r64, N, p, r32);
+            k_narrow<<<nblk(N * p), 256, 0, st>>>(r64, L, N, p, r32, L);
             VSIE_CUDA(cudaGetLastError());
             gmres_core(K32, r32, itol, budget, false, apply32_pc, e32, iters, est, cnt);
             mv32 += cnt;
             // x += M32 e
             const float2* corr = e32;
             if (use_pc) {
-                apply_block_precond<float>(c, p, e32, N, z32, N, st);
+                apply_block_precond<float>(c, p, e32, L, z32, L, st);
                 corr = z32;
             }
-            k_add_widen<<<nblk(N * p), 256, 0, st>>>(corr, N, p, X, ldx);
+            k_add_widen<<<nblk(N * p), 256, 0, st>>>(corr, L, N, p, X, ldx);
             VSIE_CUDA(cudaGetLastError());
         }
     }
     // final true FP64 residual
-    VSIE_CUDA(cudaMemcpy2DAsync(e64, N * sizeof(double2), X, ldx * sizeof(double2),
+    VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
                                 N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     apply64(e64, Ax);
     ++mv64;
-    k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, N, N, p, w64, N);
+    k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, w64, L);
     VSIE_CUDA(cudaGetLastError());
     std::vector<double> rn2;
     K64.norms(rn2);
