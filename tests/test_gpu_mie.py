@@ -1,0 +1,57 @@
+"""Solver-level check on the GPU: a homogeneous sphere under a plane wave, set
+up by vsie_setup (volume only) and solved by vsie_solve, against the oracle's
+solution of the same discrete system and against the Lorenz-Mie interior field
+(oracle/mie.py)."""
+import numpy as np
+import pytest
+from scipy.sparse.linalg import LinearOperator, gmres
+
+from oracle import mie, physics, volume
+from paper_2206_12409_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+F = 298e6
+R = 25e-3
+
+
+@pytest.mark.parametrize("N,eps,sig,mode", [(16, 2.0, 0.0, 1), (12, 50.0, 0.6, 1), (12, 50.0, 0.6, 0)])
+def test_sphere_plane_wave_vs_oracle_and_mie(N, eps, sig, mode):
+    import torch
+    from paper_2206_12409_gb300 import vsie as V
+    h = 2 * R / N
+    g, er, sg = I.sphere_phantom(n=(N + 2,) * 3, h=h, radius=R, eps_r=eps, sigma=sig)
+    prob = I.Problem("sphere", g, er, sg, F)
+    b = mie.body_rhs(g, er, sg, F)
+    # oracle solution of the same discrete system
+    chi = physics.chi(er, sg, F)
+    _, k0 = physics.omega_k0(F)
+    spec = volume.kernel_spectra(g.n, g.h, k0)
+    A = LinearOperator((3 * g.nv,) * 2, dtype=complex,
+                       matvec=lambda v: volume.fft_matvec(g, chi, k0, v, spec).ravel())
+    xo, info = gmres(A, b, rtol=1e-11, restart=200, maxiter=5000)
+    assert info == 0
+    ctx = V.setup_problem(prob, max_rhs=1)
+    try:
+        n_tot = V.vsie_sizes(ctx)[0]
+        assert n_tot == 3 * g.nv
+        B = torch.from_numpy(b.copy()).cuda()[None, :]
+        X = torch.zeros_like(B)
+        o = V.vsie_solve_opts()
+        o.mode = mode
+        o.restart = 50
+        o.maxit = 4000
+        st, info = V.vsie_solve(ctx, 1, B.data_ptr(), n_tot, X.data_ptr(), n_tot, 1e-9, o)
+        assert st == V.VSIE_OK and info.relres[0] <= 1e-9
+        x = X.cpu().numpy()[0]
+    finally:
+        V.vsie_destroy(ctx)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+    inside = chi != 0
+    req = (3 * inside.sum() * h ** 3 / (4 * np.pi)) ** (1 / 3)
+    Em = mie.interior_field(g.centres()[inside], req, eps, sig, F)
+    e_gpu = np.linalg.norm(mie.body_field(x, er, sg, F)[inside] - Em) / np.linalg.norm(Em)
+    e_or = np.linalg.norm(mie.body_field(xo, er, sg, F)[inside] - Em) / np.linalg.norm(Em)
+    assert abs(e_gpu - e_or) < 1e-5
+    # the discretisation error of the one-point body operator (staircase sphere)
+    assert e_gpu < (0.06 if eps < 10 else 0.65)
