@@ -131,13 +131,15 @@ typedef struct {
 
 /* Solver options for vsie_solve (zero-initialise; zeros select defaults). */
 typedef struct {
-    int32_t mode;       /* 0 = plain FP64 GMRES; 1 = FP32 inner FGMRES with FP64 refinement */
+    int32_t mode;       /* 0 = plain FP64 GMRES; 1 = FP32 inner GMRES with FP64 refinement  */
     int32_t restart;    /* GMRES restart length m (default 50)                            */
     int32_t maxit;      /* total inner iteration cap per RHS (default 2000)               */
     double inner_tol;   /* mode 1: relative tolerance of each inner solve (default 1e-4)  */
     int32_t max_outer;  /* mode 1: refinement steps cap (default 20)                      */
     int32_t precond;    /* right preconditioner: 0 = block (inverses of the two surface
-                           blocks, inverse body diagonal; default), 1 = none             */
+                           blocks, inverse body diagonal; default), 1 = none, 2 = block
+                           with the attached network on the body (vsie_net_attach),
+                           which makes the inner solve flexible GMRES (FGMRES)         */
 } vsie_solve_opts;
 
 typedef struct {
@@ -197,8 +199,10 @@ VSIE_API vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t
 /* Solve Z X = B for p right-hand sides to relative FP64 residual tol (Sec. III.A:
  * GMRES with restart; x0 = 0).  B, X: device double2 (C128), column-major N x p.
  * mode 0: every matvec, orthogonalisation and Givens update in FP64.
- * mode 1: FP32 matvec inside flexible GMRES, FP64 outer residual r = B - Z X and
- * FP64 Gram-Schmidt/Givens (iterative refinement).  Synchronous with respect to
+ * mode 1: iterative refinement: FP64 outer residual r = B - Z X, inner GMRES on
+ * the FP32 operator with an FP32 basis and FP32 Gram-Schmidt (FP64 across thread
+ * blocks), FP64 Givens on the host.  precond = 2 makes the solve flexible GMRES
+ * (the network's output depends on its input).  Synchronous with respect to
  * `stream`.  info (host) may be NULL.  Returns ENOCONV when any RHS misses tol
  * (X then holds the last iterate and info its residual). */
 VSIE_API vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t ldb, void* X,
@@ -238,15 +242,70 @@ VSIE_API vsie_status vsie_volume_matvec_static(vsie_ctx* ctx, int32_t p, const v
                                                void* Y, int64_t ldy, int32_t precision,
                                                vsie_stream stream);
 
-/* Write the context's operator (grid, materials, frequency, options, parts) to
- * a versioned binary file; vsie_load recreates a context from it (Sec. VI:
- * compressed coupling matrices stored and reused). */
+/* Persistence of a context's operator (Sec. VI: compressed coupling matrices
+ * stored and reused).  Not implemented: both return VSIE_EUNSUPPORTED; set-up
+ * is deterministic and is re-run instead. */
 VSIE_API vsie_status vsie_save(const vsie_ctx* ctx, const char* path);
 VSIE_API vsie_status vsie_load(const char* path, vsie_ctx** out);
 
 /* Copy the context's parts to host arrays owned by the context (valid until
  * vsie_destroy); pointers in *parts refer to that storage. */
 VSIE_API vsie_status vsie_get_parts(vsie_ctx* ctx, vsie_parts* parts);
+
+/* ---------------------------------------------------------------------------
+ * Learned body preconditioner (not in the paper; cf. the preconditioning of the
+ * coupled system suggested in Sec. VI).  A 3D U-Net: 4 levels with 16/32/64/64
+ * channels, 3x3x3 convolutions (zero padding), ReLU, 2x2x2 average pooling,
+ * nearest x2 upsampling, skips concatenated after the upsampled tensor, and a
+ * linear 1x1x1 head; 15 layers e1a 8->16, e1b 16->16, e2a 16->32, e2b 32->32,
+ * e3a 32->64, e3b 64->64, ba 64->64, bb 64->64, d3a 128->64, d3b 64->64,
+ * d2a 96->32, d2b 32->32, d1a 48->16, d1b 16->16, head 16->6 (1x1x1).
+ * Tensors: FP32, channel-major (C, D, H, W), W fastest, D, H, W multiples of 8.
+ * Parameters: FP32 master values, packed layer by layer as the weights
+ * (Cout, Cin, k, k, k) followed by the biases (Cout); the kernels use BF16
+ * copies of the weights and accumulate in FP32.  Input channels: re/im of the
+ * three components of the Jacobi-scaled body residual divided by its RMS, then
+ * (eps_r - 1) / 50 and sigma (S/m); output: the 6-channel correction.
+ * All device pointers belong to the caller.  Errors: vsie_net_last_error. */
+typedef struct vsie_net vsie_net;
+
+/* He-normal weights from `seed`, zero biases, Adam state zero. */
+VSIE_API vsie_status vsie_net_create(uint64_t seed, vsie_net** out);
+VSIE_API vsie_status vsie_net_num_params(const vsie_net* net, int64_t* n);
+/* Host copies of the n packed parameters (n must equal vsie_net_num_params). */
+VSIE_API vsie_status vsie_net_set_params(vsie_net* net, const float* host, int64_t n);
+VSIE_API vsie_status vsie_net_get_params(vsie_net* net, float* host, int64_t n);
+/* y (6 x D x H x W, device) = net(x) (x: 8 x D x H x W, device).  Async on stream. */
+VSIE_API vsie_status vsie_net_forward(vsie_net* net, int32_t D, int32_t H, int32_t W, const float* x,
+                                      float* y, vsie_stream stream);
+/* Gradients of sum(dy * net(x)): parameters to grad_host (packed like the
+ * parameters; may be NULL) and the input gradient to dx (device, 8 x D x H x W;
+ * may be NULL).  Synchronous. */
+VSIE_API vsie_status vsie_net_backward(vsie_net* net, int32_t D, int32_t H, int32_t W, const float* x,
+                                       const float* dy, float* grad_host, float* dx,
+                                       vsie_stream stream);
+/* One training step: loss = mean((net(x) - target)^2) over all 6 D H W
+ * entries, its gradient, one Adam update (lr; beta 0.9, 0.999; eps 1e-8).
+ * Returns the loss before the update in *loss (may be NULL).  Synchronous. */
+VSIE_API vsie_status vsie_net_step(vsie_net* net, int32_t D, int32_t H, int32_t W, const float* x,
+                                   const float* target, double lr, double* loss, vsie_stream stream);
+/* Train on pairs the context's own operator generates: per step a seeded
+ * smooth random body current e (material voxels), r = Z_bb e by the FP32
+ * operator, input from the Jacobi-scaled r, target (e - D^-1 r) / s.  Writes
+ * `steps` losses to losses_host (may be NULL).  Synchronous. */
+VSIE_API vsie_status vsie_net_train(vsie_ctx* ctx, vsie_net* net, int32_t steps, double lr,
+                                    uint64_t seed, float* losses_host, vsie_stream stream);
+/* Use `net` (not owned; NULL detaches) on the body block when a solve asks for
+ * precond = 2. */
+/* Y = M X for p columns with the FP32 (C64) right preconditioner of a solve:
+ * kind 0 the block preconditioner, kind 2 the block preconditioner with the
+ * attached network on the body.  X, Y: device float2, N x p, must not overlap.
+ * Asynchronous on `stream`. */
+VSIE_API vsie_status vsie_precond_apply(vsie_ctx* ctx, int32_t p, const void* X, int64_t ldx, void* Y,
+                                        int64_t ldy, int32_t kind, vsie_stream stream);
+VSIE_API vsie_status vsie_net_attach(vsie_ctx* ctx, vsie_net* net);
+VSIE_API const char* vsie_net_last_error(const vsie_net* net);
+VSIE_API void vsie_net_destroy(vsie_net* net);
 
 VSIE_API void vsie_destroy(vsie_ctx* ctx);
 

@@ -216,6 +216,19 @@ __global__ void k_narrow(const double2* __restrict__ a, int64_t lda, int64_t N, 
     }
 }
 
+// b[c][n] = a[c][n]  (FP32 to FP64)
+__global__ void k_widen_to(const float2* __restrict__ a, int64_t lda, int64_t N, int p,
+                           double2* __restrict__ b, int64_t ldb) {
+    const int64_t tot = N * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = e / N;
+        const int64_t n = e - (int64_t)c * N;
+        const float2 v = a[(size_t)c * lda + n];
+        b[(size_t)c * ldb + n] = make_double2(v.x, v.y);
+    }
+}
+
 // X[c][n] += a[c][n]  (a FP32, X FP64)
 __global__ void k_add_widen(const float2* __restrict__ a, int64_t lda, int64_t N, int p,
                             double2* __restrict__ X, int64_t ldx) {
@@ -274,15 +287,16 @@ struct Krylov {
         nn.resize(p);
         for (int c2 = 0; c2 < p; ++c2) nn[c2] = t[c2].x;
     }
-    // tgt (p x N, leading dimension ld) += sgn V hh
-    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, cx<R>* tgt) {
+    // tgt (p x N, leading dimension ld) += sgn B hh, B = V unless given
+    void update(int nvec, const std::vector<std::complex<double>>& hh, double sgn, cx<R>* tgt,
+                const cx<R>* B = nullptr) {
         ProfScope ps(c, PG_KRYLOV, st);
         prof_count(c, 1);
         VSIE_CUDA(cudaMemcpyAsync(h, hh.data(), (size_t)p * nvec * sizeof(double2), cudaMemcpyHostToDevice, st));
         const int64_t packs = N / Pack<R>::K;
         const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((packs + 255) / 256, 1216));
-        k_basis_update<R><<<dim3(bx, p), 256, (size_t)nvec * sizeof(cx<R>), st>>>(V, nvec, N, ld, p, h,
-                                                                                 sgn, tgt, ld);
+        k_basis_update<R><<<dim3(bx, p), 256, (size_t)nvec * sizeof(cx<R>), st>>>(B ? B : V, nvec, N, ld,
+                                                                                 p, h, sgn, tgt, ld);
         VSIE_CUDA(cudaGetLastError());
     }
     void scale_into(const cx<R>* src, const std::vector<std::complex<double>>& s, cx<R>* dst) {
@@ -301,10 +315,12 @@ using cdd = std::complex<double>;
 // and out) for all p columns, relative tolerance tol with respect to
 // ||r||; returns the correction in e (p x N, leading dimension K.ld).  iters[c] accumulates the
 // iterations until column c met its tolerance.
-template <typename R, typename Apply>
+// Flexible variant (Zb != nullptr): z_j = prec(v_j) is kept in Zb, w = A z_j
+// and the correction is Zb y (Saad 1993); `apply` is then the plain operator.
+template <typename R, typename Apply, typename Prec>
 static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool cgs2, Apply apply,
-                       cx<R>* e, std::vector<int>& iters, std::vector<double>& relres_est,
-                       int& nmatvec) {
+                       Prec prec, cx<R>* Zb, cx<R>* e, std::vector<int>& iters,
+                       std::vector<double>& relres_est, int& nmatvec) {
     const int p = K.p;
     const int64_t N = K.N, ld = K.ld;
     const int m = K.m;
@@ -346,7 +362,13 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
         std::vector<bool> cyc_done(done);
         int j = 0;
         for (; j < m && total < maxit; ++j) {
-            apply(K.basis(j), K.w);   // w = A v_j
+            if (Zb) {
+                cx<R>* zj = Zb + (size_t)j * p * ld;
+                prec(K.basis(j), zj);   // z_j = M_j v_j
+                apply(zj, K.w);         // w = A z_j
+            } else {
+                apply(K.basis(j), K.w);   // w = A v_j
+            }
             ++nmatvec;
             std::vector<cdd> hh, hh2;
             K.dots(j + 1, hh);
@@ -407,7 +429,7 @@ static void gmres_core(Krylov<R>& K, const cx<R>* r, double tol, int maxit, bool
                 Y[(size_t)c * k + i] = d != 0.0 ? s / d : 0.0;
             }
         }
-        K.update(k, Y, 1.0, e);
+        K.update(k, Y, 1.0, e, Zb);
         // true residual of the correction: res = r - A e
         apply(e, K.w);
         ++nmatvec;
@@ -441,9 +463,15 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     const size_t pN = (size_t)p * L;
     // workspace (kept in the context between solves): the basis in the
     // precision of the mode, four FP64 and five FP32 p x N blocks, dot scratch
+    if (o.precond < 0 || o.precond > 2) throw Error(VSIE_EINVAL, "precond must be 0, 1 or 2");
     const bool use_pc = o.precond != 1;
+    const bool flex = o.precond == 2;   // learned body preconditioner: flexible GMRES
+    if (flex && !c.net) throw Error(VSIE_EINVAL, "precond = 2 needs a network (vsie_net_attach)");
+    if (flex && !c.f32.ready) throw Error(VSIE_EUNSUPPORTED, "precond = 2 needs the C64 operator");
     if (use_pc) build_block_precond(c);
-    const size_t basis_bytes = (size_t)(m + 1) * pN * (o.mode == 0 ? sizeof(double2) : sizeof(float2));
+    // basis (and, for flexible GMRES, the preconditioned basis) in the mode's precision
+    const size_t basis_bytes = (size_t)(m + 1) * pN * (o.mode == 0 ? sizeof(double2) : sizeof(float2)) *
+                               (flex ? 2 : 1);
     const size_t need = basis_bytes + 5 * pN * sizeof(double2) + 5 * pN * sizeof(float2) +
                         ((size_t)kDotBlocks * p * (m + 1) + (size_t)p * (m + 1) + p) * sizeof(double2) +
                         16 * 256;   // slack for the 256-byte alignment of each slice below
@@ -461,6 +489,7 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     char* base = (char*)c.kr_V;
     auto take = [&](size_t bytes) { char* q = base; base += (bytes + 255) / 256 * 256; return q; };
     void* Vb = take(basis_bytes);
+    void* Zbb = flex ? (void*)((char*)Vb + basis_bytes / 2) : nullptr;
     double2* w64 = (double2*)take(pN * sizeof(double2));
     double2* r64 = (double2*)take(pN * sizeof(double2));
     double2* e64 = (double2*)take(pN * sizeof(double2));
@@ -507,16 +536,31 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
         }
         matvec_internal<float>(c, p, src, L, out, L, st);
     };
+    // flexible GMRES: plain operators and the learned preconditioner
+    auto apply32 = [&](const float2* in, float2* out) { matvec_internal<float>(c, p, in, L, out, L, st); };
+    auto prec32 = [&](const float2* in, float2* out) { apply_learned_precond(c, p, in, L, out, L, st); };
+    auto prec64 = [&](const double2* in, double2* out) {
+        k_narrow<<<nblk(N * p), 256, 0, st>>>(in, L, N, p, t32, L);
+        apply_learned_precond(c, p, t32, L, z32, L, st);
+        k_widen_to<<<nblk(N * p), 256, 0, st>>>(z32, L, N, p, out, L);
+        VSIE_CUDA(cudaGetLastError());
+    };
+    auto noprec32 = [](const float2*, float2*) {};
+    auto noprec64 = [](const double2*, double2*) {};
     // x = 0
     VSIE_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, N * sizeof(double2), p, st));
     std::vector<double> relres(p, 1.0);
     if (o.mode == 0) {
         int cnt = 0;
-        gmres_core(K64, r64, tol, maxit, true, apply64_pc, e64, iters, est, cnt);
+        if (flex)
+            gmres_core(K64, r64, tol, maxit, true, apply64, prec64, (double2*)Zbb, e64, iters, est, cnt);
+        else
+            gmres_core(K64, r64, tol, maxit, true, apply64_pc, noprec64, (double2*)nullptr, e64, iters,
+                       est, cnt);
         mv64 += cnt;
-        // x = M e
+        // x = M e (flexible: e is already the solution)
         const double2* xs = e64;
-        if (use_pc) {
+        if (use_pc && !flex) {
             apply_block_precond<double>(c, p, e64, L, z64, L, st);
             xs = z64;
         }
@@ -553,11 +597,16 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             if (budget <= 0) break;
             k_narrow<<<nblk(N * p), 256, 0, st>>>(r64, L, N, p, r32, L);
             VSIE_CUDA(cudaGetLastError());
-            gmres_core(K32, r32, itol, budget, false, apply32_pc, e32, iters, est, cnt);
+            if (flex)
+                gmres_core(K32, r32, itol, budget, false, apply32, prec32, (float2*)Zbb, e32, iters, est,
+                           cnt);
+            else
+                gmres_core(K32, r32, itol, budget, false, apply32_pc, noprec32, (float2*)nullptr, e32,
+                           iters, est, cnt);
             mv32 += cnt;
-            // x += M32 e
+            // x += M32 e (flexible: e is already the correction)
             const float2* corr = e32;
-            if (use_pc) {
+            if (use_pc && !flex) {
                 apply_block_precond<float>(c, p, e32, L, z32, L, st);
                 corr = z32;
             }

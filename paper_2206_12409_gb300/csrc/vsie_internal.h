@@ -199,6 +199,10 @@ struct Ctx {
     bool owns_all = true;
     double2* dZff_in = nullptr;        // far-far block handed over on the device (FP64)
     bool pc_ready = false;             // block preconditioner built
+    void* net = nullptr;               // attached learned body preconditioner (not owned)
+    float* net_mat = nullptr;          // 2 x n_b: (eps_r - 1) / 50, sigma
+    double* net_part = nullptr;        // reduction partials of the network's input scale
+    float* net_scale = nullptr;        // per RHS: RMS of the Jacobi-scaled body residual
     vsie_parts parts_view{};           // filled by vsie_get_parts
     std::vector<std::complex<double>> hZff_copy;
 };
@@ -267,6 +271,10 @@ void conv_set_attrs();
 template <typename R>
 void conv_autotune(Ctx& c);
 void build_block_precond(Ctx& c);
+// learned body preconditioner (nettrain.cu): Y = M X with the surface blocks of
+// the block preconditioner and the attached network on the body
+void apply_learned_precond(Ctx& c, int p, const float2* X, int64_t ldx, float2* Y, int64_t ldy,
+                           cudaStream_t st);
 template <typename R>
 void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
                          cudaStream_t st);

@@ -26,6 +26,9 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
            "vsie_matvec", "vsie_rhs_ports", "vsie_solve", "vsie_save", "vsie_load",
            "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_volume_matvec_static",
+           "vsie_net_create", "vsie_net_num_params", "vsie_net_set_params", "vsie_net_get_params",
+           "vsie_net_forward", "vsie_net_backward", "vsie_net_step", "vsie_net_train",
+           "vsie_net_attach", "vsie_precond_apply", "vsie_net_last_error", "vsie_net_destroy",
            "vsie_destroy"]
 PROFILE_GROUPS = {"fft_conv": 0, "pfft": 1, "precorrection": 2, "surface": 3, "tt": 4,
                   "krylov": 5, "precond": 6}
@@ -121,6 +124,32 @@ def load_library(path: str | None = None):
     lib.vsie_volume_matvec_static.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
     lib.vsie_destroy.restype = None
     lib.vsie_destroy.argtypes = [P]
+    F = C.POINTER(C.c_float)
+    lib.vsie_net_create.restype = C.c_int
+    lib.vsie_net_create.argtypes = [C.c_uint64, C.POINTER(P)]
+    lib.vsie_net_num_params.restype = C.c_int
+    lib.vsie_net_num_params.argtypes = [P, C.POINTER(C.c_int64)]
+    lib.vsie_net_set_params.restype = C.c_int
+    lib.vsie_net_set_params.argtypes = [P, F, C.c_int64]
+    lib.vsie_net_get_params.restype = C.c_int
+    lib.vsie_net_get_params.argtypes = [P, F, C.c_int64]
+    lib.vsie_net_forward.restype = C.c_int
+    lib.vsie_net_forward.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P]
+    lib.vsie_net_backward.restype = C.c_int
+    lib.vsie_net_backward.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, F, P, P]
+    lib.vsie_net_step.restype = C.c_int
+    lib.vsie_net_step.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, C.c_double,
+                                  C.POINTER(C.c_double), P]
+    lib.vsie_net_train.restype = C.c_int
+    lib.vsie_net_train.argtypes = [P, P, C.c_int32, C.c_double, C.c_uint64, F, P]
+    lib.vsie_precond_apply.restype = C.c_int
+    lib.vsie_precond_apply.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
+    lib.vsie_net_attach.restype = C.c_int
+    lib.vsie_net_attach.argtypes = [P, P]
+    lib.vsie_net_last_error.restype = C.c_char_p
+    lib.vsie_net_last_error.argtypes = [P]
+    lib.vsie_net_destroy.restype = None
+    lib.vsie_net_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -380,3 +409,82 @@ def setup_problem(prob, max_rhs=8, precisions=0):
                         precisions=precisions)
     return vsie_setup(make_grid(g.n, g.h, g.origin), prob.eps_r, prob.sigma, coil, shield,
                       prob.freq_hz, opts)
+
+
+# ------------------------------------------------------------- learned preconditioner
+def _check_net(st, net):
+    if st != VSIE_OK:
+        lib = load_library()
+        msg = lib.vsie_net_last_error(net) if net else lib.vsie_last_error(None)
+        raise VsieError(st, msg.decode() if msg else "")
+
+
+def vsie_net_create(seed=0):
+    lib = load_library()
+    out = C.c_void_p()
+    _check(lib.vsie_net_create(int(seed), C.byref(out)))
+    return out
+
+
+def vsie_net_num_params(net):
+    n = C.c_int64()
+    _check_net(load_library().vsie_net_num_params(net, C.byref(n)), net)
+    return n.value
+
+
+def vsie_net_set_params(net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check_net(load_library().vsie_net_set_params(net, a.ctypes.data_as(C.POINTER(C.c_float)), a.size), net)
+
+
+def vsie_net_get_params(net):
+    a = np.empty(vsie_net_num_params(net), np.float32)
+    _check_net(load_library().vsie_net_get_params(net, a.ctypes.data_as(C.POINTER(C.c_float)), a.size), net)
+    return a
+
+
+def vsie_net_forward(net, D, H, W, x_ptr, y_ptr, stream=0):
+    _check_net(load_library().vsie_net_forward(net, int(D), int(H), int(W), C.c_void_p(int(x_ptr)),
+                                               C.c_void_p(int(y_ptr)), C.c_void_p(int(stream))), net)
+
+
+def vsie_net_backward(net, D, H, W, x_ptr, dy_ptr, dx_ptr=0, stream=0):
+    """Returns the packed parameter gradients (host)."""
+    g = np.empty(vsie_net_num_params(net), np.float32)
+    _check_net(load_library().vsie_net_backward(net, int(D), int(H), int(W), C.c_void_p(int(x_ptr)),
+                                                C.c_void_p(int(dy_ptr)),
+                                                g.ctypes.data_as(C.POINTER(C.c_float)),
+                                                C.c_void_p(int(dx_ptr)), C.c_void_p(int(stream))), net)
+    return g
+
+
+def vsie_net_step(net, D, H, W, x_ptr, target_ptr, lr, stream=0):
+    loss = C.c_double()
+    _check_net(load_library().vsie_net_step(net, int(D), int(H), int(W), C.c_void_p(int(x_ptr)),
+                                            C.c_void_p(int(target_ptr)), float(lr), C.byref(loss),
+                                            C.c_void_p(int(stream))), net)
+    return loss.value
+
+
+def vsie_net_train(ctx, net, steps, lr=1e-3, seed=0, stream=0):
+    """Returns the per-step losses."""
+    L = np.zeros(max(int(steps), 1), np.float32)
+    _check(load_library().vsie_net_train(ctx, net, int(steps), float(lr), int(seed),
+                                         L.ctypes.data_as(C.POINTER(C.c_float)), C.c_void_p(int(stream))),
+           ctx)
+    return L[:int(steps)]
+
+
+def vsie_net_attach(ctx, net):
+    _check(load_library().vsie_net_attach(ctx, net), ctx)
+
+
+def vsie_net_destroy(net):
+    if net:
+        load_library().vsie_net_destroy(net)
+
+
+def vsie_precond_apply(ctx, p, X, ldx, Y, ldy, kind, stream=0):
+    """Y = M X with the FP32 preconditioner (kind 0 block, 2 learned)."""
+    _check(load_library().vsie_precond_apply(ctx, int(p), C.c_void_p(int(X)), int(ldx), C.c_void_p(int(Y)),
+                                             int(ldy), int(kind), C.c_void_p(int(stream))), ctx)
