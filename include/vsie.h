@@ -291,7 +291,8 @@ VSIE_API vsie_status vsie_net_step(vsie_net* net, int32_t D, int32_t H, int32_t 
                                    const float* target, double lr, double* loss, vsie_stream stream);
 /* Train on pairs the context's own operator generates: per step a seeded
  * smooth random body current e (material voxels), r = Z_bb e by the FP32
- * operator, input from the Jacobi-scaled r, target (e - D^-1 r) / s.  Writes
+ * operator, input from the Jacobi-scaled r, target (e - D^-1 r) / s; Adam with
+ * the learning rate decaying linearly from lr to lr / 10 over the steps.  Writes
  * `steps` losses to losses_host (may be NULL).  Synchronous. */
 VSIE_API vsie_status vsie_net_train(vsie_ctx* ctx, vsie_net* net, int32_t steps, double lr,
                                     uint64_t seed, float* losses_host, vsie_stream stream);

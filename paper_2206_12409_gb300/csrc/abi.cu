@@ -37,13 +37,15 @@ static T* upload(Ctx& c, const T* h, size_t n) {
     return d;
 }
 
-bool fft_factor(int L, FFTPlan& pl) {
+bool fft_factor(int L, FFTPlan& pl, int max_radix) {
     pl = FFTPlan();
     pl.L = L;
     if (L < 1) return false;
     int n = L, p2 = 0;
     while (n % 2 == 0) { n /= 2; ++p2; }
     std::vector<int> r;
+    if (max_radix >= 16)
+        while (p2 >= 4) { r.push_back(16); p2 -= 4; }
     while (p2 >= 3) { r.push_back(8); p2 -= 3; }
     if (p2 == 2) r.push_back(4);
     if (p2 == 1) r.push_back(2);
@@ -204,7 +206,16 @@ static void init_ctx(Ctx& c, const vsie_grid* body, const double* eps_r, const d
     for (int i = 0; i < 3; ++i) {
         c.L[i] = next_smooth(2 * c.ne[i] - 1);
         c.Lh[i] = c.L[i] / 2 + 1;
-        if (!fft_factor(c.L[i], c.plan[i])) throw Error(VSIE_EUNSUPPORTED, "FFT length");
+        if (!fft_factor(c.L[i], c.plan[i], 8) || !fft_factor(c.L[i], c.plan16[i], 16))
+            throw Error(VSIE_EUNSUPPORTED, "FFT length");
+    }
+    // half-length plans of the third axis (Z pass), twiddles read from the L3 table
+    if (c.L[2] % 2 == 0 && fft_factor(c.L[2] / 2, c.plan3h, 8) && fft_factor(c.L[2] / 2, c.plan3h16, 16)) {
+        for (int s2 = 0; s2 < c.plan3h.nst; ++s2) c.plan3h.twstep[s2] *= 2;
+        for (int s2 = 0; s2 < c.plan3h16.nst; ++s2) c.plan3h16.twstep[s2] *= 2;
+    } else {
+        c.plan3h = FFTPlan();
+        c.plan3h16 = FFTPlan();
     }
     c.eps_r.assign(eps_r, eps_r + c.n_b);
     c.sigma.assign(sigma, sigma + c.n_b);

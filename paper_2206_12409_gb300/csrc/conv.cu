@@ -43,6 +43,8 @@ struct ConvArgs {
     const cx<R>* tw2;
     const cx<R>* tw3;
     FFTPlan pl1, pl2, pl3;
+    FFTPlan pl3h;   // length L3 / 2, twiddle steps indexing the L3 table (L3 even)
+    int zhalf;      // 1: the Z pass runs on half-length transforms
 };
 
 // x / d given magic = magic_div(d); magic 0 encodes d == 1
@@ -253,6 +255,99 @@ __global__ void __launch_bounds__(1024) k_zmul(ConvArgs<R> a) {
     }
 }
 
+// --------------------------------------------------------------- Z fused, half length
+// For even L3 = 2M (then n3 <= M): with w = exp(-2 pi i / L3) and x zero beyond
+// n3, the length-L3 transform splits into X[2k] = FFT_M(x)[k] and
+// X[2k+1] = FFT_M(x w^n)[k], and the unnormalised inverse on n < n3 is
+// IFFT_M(X_even)[n] + w^-n IFFT_M(X_odd)[n].  The zero half of every line is
+// never stored or transformed, and the transforms are half as long.
+// Shared memory: the L3 twiddles, then 2 x 3 NL lines of length M (even-part
+// lines first) and their ping-pong scratch.
+template <typename R, int NL>
+__global__ void __launch_bounds__(1024) k_zmul_h(ConvArgs<R> a) {
+    using C = cx<R>;
+    constexpr int NLT = 3 * NL, NL2 = 2 * NLT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    const int M = a.L3 / 2;
+    C* buf = tw + a.L3;
+    C* scr = buf + (size_t)M * NL2;
+    const int k10 = blockIdx.x * NL, j = blockIdx.z;
+    // visit k2 and its mirror L2 - k2 back to back (they share spectrum octants)
+    const int y = blockIdx.y;
+    const int k2 = y == 0 ? 0 : ((y & 1) ? (y + 1) >> 1 : a.L2 - (y >> 1));
+    load_tw(tw, a.tw3, a.L3);
+    __syncthreads();
+    const size_t plane = (size_t)a.L2 * a.L1;
+    const C* in = a.B + (size_t)j * 3 * a.n3 * plane + (size_t)k2 * a.L1;
+    const size_t cstride = (size_t)a.n3 * plane;
+    constexpr int U = 8;
+    const int tot = NLT * M;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int ln = e % NLT, k3 = e / NLT;
+            const int comp = ln / NL, l = ln - comp * NL;
+            const int k1 = k10 + l;
+            v[u] = czero<C>();
+            if (e < tot && k3 < a.n3 && k1 < a.L1) v[u] = in[comp * cstride + (size_t)k3 * plane + k1];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < tot) {
+                const int ln = e % NLT, k3 = e / NLT;
+                buf[k3 * NL2 + ln] = v[u];
+                buf[k3 * NL2 + NLT + ln] = cmul(v[u], tw[k3]);
+            }
+        }
+    }
+    __syncthreads();
+    {
+        C* r = fft_pp<false, NL2, NL2>(buf, scr, a.pl3h, tw);
+        if (r != buf) { scr = buf; buf = r; }
+    }
+    {
+        const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
+        const int kk2 = k2 <= a.L2 / 2 ? k2 : a.L2 - k2;
+        const R sg2 = k2 <= a.L2 / 2 ? (R)1 : (R)-1;
+        for (int e = threadIdx.x; e < NL * a.L3; e += blockDim.x) {
+            const int l = e % NL, k3 = e / NL;
+            const int k1 = k10 + l;
+            if (k1 >= a.L1) continue;
+            const int kk1 = k1 <= a.L1 / 2 ? k1 : a.L1 - k1;
+            const R sg1 = k1 <= a.L1 / 2 ? (R)1 : (R)-1;
+            const int kk3 = k3 <= a.L3 / 2 ? k3 : a.L3 - k3;
+            const R sg3 = k3 <= a.L3 / 2 ? (R)1 : (R)-1;
+            const size_t o = kk1 + (size_t)a.Lh1 * (kk2 + (size_t)a.Lh2 * kk3);
+            const C txx = a.spec[o], tyy = a.spec[oct + o], tzz = a.spec[2 * oct + o];
+            const C txy = cscale(a.spec[3 * oct + o], sg1 * sg2);
+            const C txz = cscale(a.spec[4 * oct + o], sg1 * sg3);
+            const C tyz = cscale(a.spec[5 * oct + o], sg2 * sg3);
+            C* px = buf + (size_t)(k3 >> 1) * NL2 + (k3 & 1) * NLT + l;
+            const C x = px[0], yv = px[NL], z = px[2 * NL];
+            C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
+            cfma(ox, txy, yv); cfma(ox, txz, z);
+            cfma(oy, tyy, yv); cfma(oy, tyz, z);
+            cfma(oz, tyz, yv); cfma(oz, tzz, z);
+            px[0] = ox; px[NL] = oy; px[2 * NL] = oz;
+        }
+    }
+    __syncthreads();
+    const C* res = fft_pp<true, NL2, NL2>(buf, scr, a.pl3h, tw);
+    C* out = a.B + (size_t)j * 3 * a.n3 * plane + (size_t)k2 * a.L1;
+    for (int e = threadIdx.x; e < NLT * a.n3; e += blockDim.x) {
+        const int ln = e % NLT, k3 = e / NLT;
+        const int comp = ln / NL, l = ln - comp * NL;
+        const int k1 = k10 + l;
+        if (k1 < a.L1)
+            out[comp * cstride + (size_t)k3 * plane + k1] =
+                cadd(res[k3 * NL2 + ln], cmulc(res[k3 * NL2 + NLT + ln], tw[k3]));
+    }
+}
+
 // --------------------------------------------------------------- X inverse + epilogue
 template <typename R, int NL>
 __global__ void __launch_bounds__(1024) k_xinv(ConvArgs<R> a) {
@@ -362,7 +457,10 @@ static ConvArgs<R> make_args(Ctx& c, const cx<R>* X, int64_t ldx, cx<R>* Y, int6
     a.line_flag = c.body_lines;
     a.gc = d.gc; a.cc = d.cc; a.A = d.bufA; a.B = d.bufB;
     a.spec = d.spec; a.tw1 = d.tw[0]; a.tw2 = d.tw[1]; a.tw3 = d.tw[2];
-    a.pl1 = c.plan[0]; a.pl2 = c.plan[1]; a.pl3 = c.plan[2];
+    const FFTPlan* pl = sizeof(R) == 4 ? c.plan16 : c.plan;
+    a.pl1 = pl[0]; a.pl2 = pl[1]; a.pl3 = pl[2];
+    a.pl3h = sizeof(R) == 4 ? c.plan3h16 : c.plan3h;
+    a.zhalf = sizeof(R) == 4 && c.L[2] % 2 == 0 && a.pl3h.L == c.L[2] / 2 ? 1 : 0;
     return a;
 }
 
@@ -384,6 +482,12 @@ template <typename R, int NL>
 static void launch_z(const ConvArgs<R>& a, int p, int t, cudaStream_t st) {
     const size_t sm = (size_t)a.L3 * (6 * NL + 1) * sizeof(cx<R>);
     dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
+    if constexpr (sizeof(R) == 4) {   // FP32 only: the FP64 variant would spill
+        if (a.zhalf) {
+            k_zmul_h<R, NL><<<g, t, sm, st>>>(a);
+            return;
+        }
+    }
     k_zmul<R, NL><<<g, t, sm, st>>>(a);
 }
 

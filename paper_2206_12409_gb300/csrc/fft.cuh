@@ -135,6 +135,45 @@ __device__ __forceinline__ void dft_odd(C* v) {
         v[RR - q] = csub(re, ri);
     }
 }
+// a * exp(-+ i theta) with c = cos theta, s = sin theta (forward: minus)
+template <bool INV, typename C, typename R>
+__device__ __forceinline__ C twc(C a, R c, R s) {
+    C r;
+    if (INV) { r.x = a.x * c - a.y * s; r.y = a.y * c + a.x * s; }
+    else { r.x = a.x * c + a.y * s; r.y = a.y * c - a.x * s; }
+    return r;
+}
+
+// radix 16 as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2,
+// X[k1 + 4 k2] = sum_n2 w4^(n2 k2) w16^(n2 k1) sum_n1 w4^(n1 k1) x[4 n1 + n2]
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<16>) {
+    using R = decltype(v[0].x);
+    constexpr R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173;
+    constexpr R q = (R)0.70710678118654752440;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    // y[n2][k1] at v[n2 + 4 k1]; twiddle by w16^(n2 k1)
+    v[5] = twc<INV>(v[5], c1, s1);       // n2 1, k1 1: w^1
+    v[9] = twc<INV>(v[9], q, q);         // n2 1, k1 2: w^2
+    v[13] = twc<INV>(v[13], s1, c1);     // n2 1, k1 3: w^3
+    v[6] = twc<INV>(v[6], q, q);         // n2 2, k1 1: w^2
+    v[10] = rot90<INV>(v[10]);           // n2 2, k1 2: w^4
+    v[14] = twc<INV>(v[14], -q, q);      // n2 2, k1 3: w^6
+    v[7] = twc<INV>(v[7], s1, c1);       // n2 3, k1 1: w^3
+    v[11] = twc<INV>(v[11], -q, q);      // n2 3, k1 2: w^6
+    v[15] = twc<INV>(v[15], -c1, -s1);   // n2 3, k1 3: w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4 x 4 block
+    C t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<5>) { dft_odd<INV, 5>(v); }
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<7>) { dft_odd<INV, 7>(v); }
 
@@ -177,6 +216,11 @@ __device__ C* fft_pp(C* a, C* b, const FFTPlan& pl, const C* tw) {
         const uint32_t mg = pl.nsmagic[st];
         const int ts = pl.twstep[st];
         switch (pl.rad[st]) {
+            case 16:
+                // radix 16 is planned for FP32 only (FP64 plans stop at 8, keeping the
+                // FP64 kernels' registers within their launch bounds)
+                if constexpr (sizeof(C) == 8) stage_pp<16, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw);
+                break;
             case 8: stage_pp<8, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
             case 4: stage_pp<4, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;
             case 2: stage_pp<2, INV, NLT, KS>(src, dst, pl.L, Ns, mg, ts, tw); break;

@@ -318,7 +318,9 @@ vsie_status vsie_net_train(vsie_ctx* ctx, vsie_net* net, int32_t steps, double l
             k_target<<<g1((int64_t)W * H * D), 256, 0, st>>>(e, Y + off, d.pc_bdiag, c.net_scale, n1, n2, n3, W, H,
                                                              D, net_target(nt));
             VSIE_CUDA(cudaGetLastError());
-            const double L = net_train_on_target(nt, (float)lr, st);
+            // learning rate decays linearly to a tenth over the run
+            const double lr_s = lr * (1.0 - 0.9 * (double)s / (double)std::max(steps, 1));
+            const double L = net_train_on_target(nt, (float)lr_s, st);
             if (losses_host) losses_host[s] = (float)L;
         }
         VSIE_CUDA(cudaStreamSynchronize(st));

@@ -83,7 +83,9 @@ __host__ __device__ inline uint32_t magic_div(uint32_t d) {
     return d <= 1 ? 0u : (uint32_t)((0x100000000ull / d) + 1ull);
 }
 
-bool fft_factor(int L, FFTPlan& plan);     // radices 8,4,2,3,5,7; false if L not 7-smooth
+// radices (16,) 8, 4, 2, 3, 5, 7 with the largest power-of-two radix max_radix;
+// false if L is not 7-smooth
+bool fft_factor(int L, FFTPlan& plan, int max_radix);
 int next_smooth(int n);                    // smallest 7-smooth integer >= n
 
 // ----------------------------------------------------------------- device buffers
@@ -155,7 +157,9 @@ struct Ctx {
     int max_rhs = 16;
     int precisions = 3;
     vsie_options opts{};
-    FFTPlan plan[3];
+    FFTPlan plan[3];            // radices up to 8 (FP64 kernels, spectra set-up)
+    FFTPlan plan16[3];          // radices up to 16 (FP32 convolution kernels)
+    FFTPlan plan3h, plan3h16;   // length L3 / 2 (twiddle steps into the L3 table), L3 even
     int L[3] = {0, 0, 0}, Lh[3] = {0, 0, 0};   // FFT lengths and octant sizes (L/2 + 1)
     // host copies (for save / get_parts / setup bookkeeping)
     std::vector<double> eps_r, sigma;

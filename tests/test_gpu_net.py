@@ -145,7 +145,7 @@ def test_trained_network_reduces_iterations_on_held_out_phantom():
     net = V.vsie_net_create(3)
     try:
         st0, it0, rr0 = _solve(V, torch, cb, pb, 0)
-        L = V.vsie_net_train(ca, net, 3000, lr=1e-3, seed=5)
+        L = V.vsie_net_train(ca, net, 6000, lr=1e-3, seed=5)
         assert np.mean(L[-50:]) < 0.6 * np.mean(L[:50])
         V.vsie_net_attach(cb, net)
         st1, it1, rr1 = _solve(V, torch, cb, pb, 2)
