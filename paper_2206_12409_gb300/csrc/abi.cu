@@ -137,6 +137,8 @@ static void prepare_precision(Ctx& c) {
         } else {
             d.Zff = up_c<R>(c, c.hZff);
         }
+        // FP32: row-panel storage for the streamed product (gemm_panel)
+        if constexpr (sizeof(R) == 4) d.Zff = to_panel(c, d.Zff, c.m_f, c.m_f);
         if (c.aca_rank > 0 && c.m_n > 0) {
             d.U = up_c<R>(c, c.hU);
             d.V = up_c<R>(c, c.hV);

@@ -7,6 +7,8 @@
 // maskC leaves masked C elements untouched.
 #include "vsie_internal.h"
 
+#include <algorithm>
+
 namespace vsie {
 
 constexpr int BK = 16;
@@ -298,5 +300,138 @@ template void cgemm<double>(Ctx&, GemmOp, int, int, int, double2, const double2*
                             int64_t, const double2*, int64_t, int64_t, double2, double2*,
                             int64_t, int64_t, int, const uint8_t*, const uint8_t*,
                             cudaStream_t);
+
+// ------------------------------------------------------------------ row panels
+// Dense FP32 blocks that are streamed every iteration (Z_ff and its inverse) are
+// stored as row panels: element (m, k) at ((m / 256) K + k) 256 + m % 256, so a
+// CTA that owns 256 rows reads one contiguous stretch of memory.  Rows past M
+// in the last panel are zero.
+constexpr int kPanel = 256;
+
+size_t panel_elems(int M, int K) { return (size_t)((M + kPanel - 1) / kPanel) * kPanel * (size_t)K; }
+
+__global__ void k_to_panel(const float2* __restrict__ A, int64_t lda, int M, int K, float2* __restrict__ P) {
+    const int mp = (M + kPanel - 1) / kPanel;
+    const size_t n = (size_t)mp * kPanel * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i % kPanel);
+        const size_t t = i / kPanel;
+        const int k = (int)(t % K), pn = (int)(t / K);
+        const int m = pn * kPanel + r;
+        P[i] = m < M ? A[(size_t)m + (size_t)k * lda] : make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void k_from_panel(const float2* __restrict__ P, int M, int K, float2* __restrict__ A, int64_t lda) {
+    const size_t n = (size_t)M * K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i % M), k = (int)(i / M);
+        A[(size_t)m + (size_t)k * lda] = P[((size_t)(m / kPanel) * K + k) * kPanel + m % kPanel];
+    }
+}
+
+// Partial products of C = P B over one K split, one thread per row, N <= NB
+// columns, with the three-multiplication complex product (Gauss):
+//   (a + ib)(c + id) = [c(a + b) - b(c + d)] + i [c(a + b) + a(d - c)],
+// the B-side sums c, d - c, c + d staged in shared memory once per K chunk.
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_gemm_panel(int M, int N, int K, const float2* __restrict__ P, const float2* __restrict__ B, int64_t ldb,
+             int splits, float2* __restrict__ ws, float2* __restrict__ C, int64_t ldc) {
+    constexpr int KC = 64, KU = 8;
+    __shared__ float Bs[KC][3][NB];
+    const int m = blockIdx.x * kPanel + threadIdx.x;
+    const int sp = blockIdx.y;
+    const int kper = (((K + splits - 1) / splits) + KC - 1) / KC * KC;
+    const int k0 = sp * kper, k1 = min(K, k0 + kper);
+    float s1[NB], s2[NB], s3[NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n) { s1[n] = 0.f; s2[n] = 0.f; s3[n] = 0.f; }
+    const float2* Ab = P + (size_t)blockIdx.x * K * kPanel + threadIdx.x;
+    for (int kc = k0; kc < k1; kc += KC) {
+        const int kn = min(KC, k1 - kc);
+        __syncthreads();
+        for (int e = threadIdx.x; e < KC * NB; e += blockDim.x) {
+            const int kk = e / NB, n = e - kk * NB;
+            const float2 b = (kk < kn && n < N) ? B[(size_t)(kc + kk) + (size_t)n * ldb] : make_float2(0.f, 0.f);
+            Bs[kk][0][n] = b.x;
+            Bs[kk][1][n] = b.y - b.x;
+            Bs[kk][2][n] = b.x + b.y;
+        }
+        __syncthreads();
+        const float2* Ap = Ab + (size_t)kc * kPanel;
+        for (int kk0 = 0; kk0 < kn; kk0 += KU) {
+            float2 a[KU];
+#pragma unroll
+            for (int u = 0; u < KU; ++u)
+                a[u] = (kk0 + u < kn) ? Ap[(size_t)(kk0 + u) * kPanel] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const float sa = a[u].x + a[u].y;
+#pragma unroll
+                for (int n = 0; n < NB; ++n) {
+                    s1[n] = fmaf(sa, Bs[kk0 + u][0][n], s1[n]);
+                    s2[n] = fmaf(a[u].x, Bs[kk0 + u][1][n], s2[n]);
+                    s3[n] = fmaf(a[u].y, Bs[kk0 + u][2][n], s3[n]);
+                }
+            }
+        }
+    }
+    if (m >= M) return;
+    if (splits == 1) {
+#pragma unroll
+        for (int n = 0; n < NB; ++n)
+            if (n < N) C[(size_t)m + (size_t)n * ldc] = make_float2(s1[n] - s3[n], s1[n] + s2[n]);
+        return;
+    }
+    float2* w = ws + (size_t)sp * M * N;
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+        if (n < N) w[(size_t)m + (size_t)M * n] = make_float2(s1[n] - s3[n], s1[n] + s2[n]);
+}
+
+void gemm_panel(Ctx& c, int M, int N, int K, const float2* P, const float2* B, int64_t ldb, float2* C,
+                int64_t ldc, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    OpData<float>& d = data<float>(c);
+    const int mb = (M + kPanel - 1) / kPanel;
+    for (int n0 = 0; n0 < N; n0 += 16) {
+        const int nn = std::min(16, N - n0);
+        int splits = std::max(1, std::min(16, K / 256));
+        while (splits > 1 && (size_t)splits * M * nn > d.splitk_elems) --splits;
+        dim3 g(mb, splits);
+        prof_count(c, splits > 1 ? 2 : 1);
+        if (nn <= 8)
+            k_gemm_panel<8><<<g, kPanel, 0, st>>>(M, nn, K, P, B + (size_t)n0 * ldb, ldb, splits, d.splitk,
+                                                C + (size_t)n0 * ldc, ldc);
+        else
+            k_gemm_panel<16><<<g, kPanel, 0, st>>>(M, nn, K, P, B + (size_t)n0 * ldb, ldb, splits, d.splitk,
+                                                 C + (size_t)n0 * ldc, ldc);
+        if (splits > 1) {
+            const size_t tot = (size_t)M * nn;
+            const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+            k_splitk_reduce<float><<<blocks, 256, 0, st>>>(M, nn, 1, splits, make_float2(1.f, 0.f), d.splitk,
+                                                           make_float2(0.f, 0.f), C + (size_t)n0 * ldc, ldc, 0,
+                                                           nullptr);
+        }
+    }
+    VSIE_CUDA(cudaGetLastError());
+}
+
+float2* to_panel(Ctx& c, float2* A, int M, int K) {
+    float2* P = (float2*)dalloc(c, panel_elems(M, K) * sizeof(float2));
+    k_to_panel<<<152 * 16, 256>>>(A, M, M, K, P);
+    VSIE_CUDA(cudaGetLastError());
+    VSIE_CUDA(cudaDeviceSynchronize());
+    auto& al = c.allocs;
+    al.erase(std::remove(al.begin(), al.end(), (void*)A), al.end());
+    cudaFree(A);
+    return P;
+}
+
+void from_panel(const float2* P, int M, int K, float2* A) {
+    k_from_panel<<<152 * 16, 256>>>(P, M, K, A, M);
+    VSIE_CUDA(cudaGetLastError());
+}
 
 }  // namespace vsie

@@ -108,12 +108,12 @@ void build_block_precond(Ctx& c) {
     if (c.m_f > 0) {
         const size_t nn = (size_t)c.m_f * c.m_f;
         float2* A = (float2*)dalloc(c, nn * sizeof(float2));
-        VSIE_CUDA(cudaMemcpy(A, c.f32.Zff, nn * sizeof(float2), cudaMemcpyDeviceToDevice));
+        from_panel(c.f32.Zff, c.m_f, c.m_f, A);     // the FP32 Z_ff is stored in row panels
         invert_f32(c, A, c.m_f);
-        c.f32.pc_Zffi = A;
         c.f64.pc_Zffi = (double2*)dalloc(c, nn * sizeof(double2));
         k_f32_widen<<<2048, 256>>>(A, c.f64.pc_Zffi, nn);
         VSIE_CUDA(cudaGetLastError());
+        c.f32.pc_Zffi = to_panel(c, A, c.m_f, c.m_f);   // frees A
     }
     if (c.m_n > 0) {
         const int mn = c.m_n;
@@ -177,9 +177,13 @@ void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, i
     ProfScope ps(c, PG_PRECOND, st);
     prof_count(c, 1);
     const cx<R> one = mk<cx<R>>(1, 0), zero = mk<cx<R>>(0, 0);
-    if (c.m_f > 0)
-        cgemm<R>(c, OP_N, c.m_f, p, c.m_f, one, d.pc_Zffi, c.m_f, 0, X, ldx, 0, zero, Y, ldy, 0, 1,
-                 nullptr, nullptr, st);
+    if (c.m_f > 0) {
+        if constexpr (sizeof(R) == 4)
+            gemm_panel(c, c.m_f, p, c.m_f, d.pc_Zffi, X, ldx, Y, ldy, st);   // FP32: row panels
+        else
+            cgemm<R>(c, OP_N, c.m_f, p, c.m_f, one, d.pc_Zffi, c.m_f, 0, X, ldx, 0, zero, Y, ldy, 0, 1,
+                     nullptr, nullptr, st);
+    }
     if (c.m_n > 0)
         cgemm<R>(c, OP_N, c.m_n, p, c.m_n, one, d.pc_Znni, c.m_n, 0, X + c.m_f, ldx, 0, zero,
                  Y + c.m_f, ldy, 0, 1, nullptr, nullptr, st);

@@ -125,8 +125,11 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
     if (mf > 0) {
         {
         ProfScope ps(c, PG_SURF, st);
-        cgemm<R>(c, OP_N, mf, p, mf, one, d.Zff, mf, 0, X, ldx, 0, zero, Y, ldy, 0, 1, nullptr,
-                 nullptr, st);
+        if constexpr (sizeof(R) == 4)
+            gemm_panel(c, mf, p, mf, d.Zff, X, ldx, Y, ldy, st);   // FP32 Z_ff in row panels
+        else
+            cgemm<R>(c, OP_N, mf, p, mf, one, d.Zff, mf, 0, X, ldx, 0, zero, Y, ldy, 0, 1, nullptr,
+                     nullptr, st);
         if (mn > 0 && c.aca_rank > 0) {
             const int k = c.aca_rank;
             // t = V^H x_f (k x p); y_n += U t

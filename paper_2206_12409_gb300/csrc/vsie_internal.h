@@ -275,6 +275,13 @@ void conv_set_attrs();
 template <typename R>
 void conv_autotune(Ctx& c);
 void build_block_precond(Ctx& c);
+// FP32 row-panel storage of the dense far blocks (gemm.cu): C = P B for
+// N right-hand sides; to_panel converts a column-major M x K matrix (lda = M,
+// freed) into a new panel allocation; from_panel writes it back column-major.
+void gemm_panel(Ctx& c, int M, int N, int K, const float2* P, const float2* B, int64_t ldb, float2* C,
+                int64_t ldc, cudaStream_t st);
+float2* to_panel(Ctx& c, float2* A, int M, int K);
+void from_panel(const float2* P, int M, int K, float2* A);
 // learned body preconditioner (nettrain.cu): Y = M X with the surface blocks of
 // the block preconditioner and the attached network on the body
 void apply_learned_precond(Ctx& c, int p, const float2* X, int64_t ldx, float2* Y, int64_t ldy,
