@@ -214,11 +214,11 @@ VSIE_API vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t
  * (0 stops recording; launch counts are always kept).  vsie_profile_query
  * synchronises the device and returns, for a group, the summed event time in
  * ms, the number of kernel launches and the algorithmic bytes moved (defined
- * for group 0 only: 54 complex values per extended-grid voxel and RHS plus the
- * spectrum octants).  Groups: 0 FFT convolution (K1), 1 pFFT projection and
- * interpolation, 2 precorrection, 3 dense and low-rank surface blocks, 4 TT
- * chain, 5 Krylov vector kernels, 6 block preconditioner; group -1 returns the
- * launches of all groups. */
+ * for groups 0 and 7 only: 54 complex values per extended-grid voxel and RHS
+ * plus the spectrum octants).  Groups: 0 FFT convolution (K1) in FP32 (C64),
+ * 1 pFFT projection and interpolation, 2 precorrection, 3 dense and low-rank
+ * surface blocks, 4 TT chain, 5 Krylov vector kernels, 6 preconditioner, 7 FFT
+ * convolution in FP64 (C128); group -1 returns the launches of all groups. */
 VSIE_API vsie_status vsie_profile(vsie_ctx* ctx, int32_t enable);
 VSIE_API vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms, int64_t* launches,
                                         double* alg_bytes);

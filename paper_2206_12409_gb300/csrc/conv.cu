@@ -433,8 +433,11 @@ __global__ void __launch_bounds__(1024) k_xinv(ConvArgs<R> a) {
 // autotuner (conv_autotune) times them on the context's own buffers and keeps
 // the fastest per pass.
 struct Variant { int nl, threads; };
-static const Variant kXV[] = {{8, 256}, {16, 256}, {16, 512}, {32, 512}, {32, 1024}};
-static const Variant kZV[] = {{4, 256}, {4, 512}, {8, 512}, {8, 1024}, {16, 1024}};
+// (thread counts that match a stage's butterfly count, e.g. 16 per line for
+// radix 16 on 256 points and 16 per half-line for radix 7 on 112 points, keep
+// every thread busy in that stage)
+static const Variant kXV[] = {{8, 128}, {8, 256}, {16, 256}, {16, 512}, {32, 512}, {32, 1024}};
+static const Variant kZV[] = {{4, 256}, {4, 384}, {4, 512}, {8, 512}, {8, 768}, {8, 1024}, {16, 1024}};
 constexpr int kNX = sizeof(kXV) / sizeof(kXV[0]);
 constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
 
@@ -536,7 +539,7 @@ void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ld
     // 54 n_v complex values per RHS, plus the 6 spectrum octants once
     const double cs = sizeof(cx<R>);
     const double alg = 54.0 * (double)c.n_e * cs * p + 6.0 * (double)c.Lh[0] * c.Lh[1] * c.Lh[2] * cs;
-    ProfScope ps(c, PG_FFTCONV, st, alg);
+    ProfScope ps(c, sizeof(R) == 4 ? PG_FFTCONV : PG_FFTCONV64, st, alg);
     const int* tune = data<R>(c).tune;
     for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, p, pass, tune[pass], st);
     prof_count(c, 5);

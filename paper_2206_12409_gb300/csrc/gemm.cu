@@ -247,6 +247,99 @@ static void launch(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> al
     VSIE_CUDA(cudaGetLastError());
 }
 
+// Inner-product shape C = alpha op(A) B (+ beta C) for op(A) in {T, H}, A stored
+// K x M column-major with few columns (M <= 512), long K, N <= NB: a CTA owns
+// IPC columns of A and one K split, its threads stride over K (coalesced reads
+// of the A columns and of B), and the sums reduce by warp shuffles.
+template <typename R, int NB, int IPC>
+__global__ void __launch_bounds__(256)
+k_gemm_ip(int conjA, int M, int N, int K, const cx<R>* __restrict__ A, int64_t lda,
+          const cx<R>* __restrict__ B, int64_t ldb, int splits, cx<R>* __restrict__ ws, cx<R> alpha,
+          cx<R> beta, cx<R>* __restrict__ C, int64_t ldc) {
+    using Cx = cx<R>;
+    const int i0 = blockIdx.x * IPC, sp = blockIdx.y;
+    const int kper = (K + splits - 1) / splits;
+    const int k0 = sp * kper, k1 = min(K, k0 + kper);
+    Cx acc[IPC][NB];
+#pragma unroll
+    for (int q = 0; q < IPC; ++q)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) acc[q][n] = czero<Cx>();
+    for (int m = k0 + threadIdx.x; m < k1; m += blockDim.x) {
+        Cx a[IPC];
+#pragma unroll
+        for (int q = 0; q < IPC; ++q) {
+            a[q] = i0 + q < M ? A[(size_t)m + (size_t)(i0 + q) * lda] : czero<Cx>();
+            if (conjA) a[q].y = -a[q].y;
+        }
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            if (n >= N) break;
+            const Cx b = B[(size_t)m + (size_t)n * ldb];
+#pragma unroll
+            for (int q = 0; q < IPC; ++q) cfma(acc[q][n], a[q], b);
+        }
+    }
+    __shared__ Cx red[IPC][NB][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < IPC; ++q)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            if (n >= N) break;
+            auto vx = acc[q][n].x, vy = acc[q][n].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vx += __shfl_down_sync(0xffffffffu, vx, o);
+                vy += __shfl_down_sync(0xffffffffu, vy, o);
+            }
+            if (lane == 0) { red[q][n][wid].x = vx; red[q][n][wid].y = vy; }
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < IPC * N; e += blockDim.x) {
+        const int q = e / N, n = e - q * N;
+        const int i = i0 + q;
+        if (i >= M) continue;
+        Cx s = czero<Cx>();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[q][n][w]);
+        if (splits > 1) {
+            ws[(size_t)sp * M * N + i + (size_t)M * n] = s;
+        } else {
+            Cx* cp = C + i + (size_t)n * ldc;
+            Cx r = cmul(alpha, s);
+            if (beta.x != 0 || beta.y != 0) cfma(r, beta, *cp);
+            *cp = r;
+        }
+    }
+}
+
+template <typename R>
+static void launch_ip(Ctx& c, bool conjA, int M, int N, int K, cx<R> alpha, const cx<R>* A, int64_t lda,
+                      const cx<R>* B, int64_t ldb, cx<R> beta, cx<R>* C, int64_t ldc, cudaStream_t st) {
+    OpData<R>& d = data<R>(c);
+    // columns per CTA: 64 accumulator words per thread at most
+    const int ipc = N <= 8 ? (sizeof(R) == 4 ? 4 : 2) : (sizeof(R) == 4 ? 2 : 1);
+    const int mb = (M + ipc - 1) / ipc;
+    int splits = std::max(1, std::min((2 * 152 + mb - 1) / mb, K / 512));
+    while (splits > 1 && (size_t)splits * M * N > d.splitk_elems) --splits;
+    dim3 g(mb, splits);
+    prof_count(c, splits > 1 ? 2 : 1);
+    const int cj = conjA ? 1 : 0;
+    if (N <= 8) {
+        if (sizeof(R) == 4) k_gemm_ip<R, 8, 4><<<g, 256, 0, st>>>(cj, M, N, K, A, lda, B, ldb, splits, d.splitk, alpha, beta, C, ldc);
+        else k_gemm_ip<R, 8, 2><<<g, 256, 0, st>>>(cj, M, N, K, A, lda, B, ldb, splits, d.splitk, alpha, beta, C, ldc);
+    } else {
+        if (sizeof(R) == 4) k_gemm_ip<R, 16, 2><<<g, 256, 0, st>>>(cj, M, N, K, A, lda, B, ldb, splits, d.splitk, alpha, beta, C, ldc);
+        else k_gemm_ip<R, 16, 1><<<g, 256, 0, st>>>(cj, M, N, K, A, lda, B, ldb, splits, d.splitk, alpha, beta, C, ldc);
+    }
+    if (splits > 1) {
+        const size_t tot = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+        k_splitk_reduce<R><<<blocks, 256, 0, st>>>(M, N, 1, splits, alpha, d.splitk, beta, C, ldc, 0, nullptr);
+    }
+    VSIE_CUDA(cudaGetLastError());
+}
+
 template <typename R>
 void cgemm2(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
             int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta, cx<R>* C,
@@ -257,8 +350,13 @@ void cgemm2(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, co
         // C = beta C
         if (beta.x == 1 && beta.y == 0) return;
     }
+    if (batch == 1 && opB == OP_N && (opA == OP_T || opA == OP_H) && !maskB && !maskC &&
+        M <= 8192 && K >= 1024 && N <= 16) {
+        launch_ip<R>(c, opA == OP_H, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+        return;
+    }
     if (batch == 1 && opB == OP_N && (opA == OP_N || opA == OP_R) && !maskB && !maskC &&
-        M >= 1024 && K >= 256 && N <= 16) {
+        M >= 1024 && N <= 16) {
         if (N <= 8)
             launch_ts<R, 8>(c, opA == OP_R, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
         else

@@ -550,6 +550,7 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
     // x = 0
     VSIE_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, N * sizeof(double2), p, st));
     std::vector<double> relres(p, 1.0);
+    bool have_res = false;
     if (o.mode == 0) {
         int cnt = 0;
         if (flex)
@@ -568,13 +569,18 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
                                     N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
     } else {
         for (outer = 0; outer < max_outer; ++outer) {
-            // r = b - Z64 x
-            VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
-                                        N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
-            apply64(e64, Ax);
-            ++mv64;
-            k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, r64, L);
-            VSIE_CUDA(cudaGetLastError());
+            // r = b - Z64 x  (x = 0 on the first pass: r = b, no matvec)
+            if (outer == 0) {
+                VSIE_CUDA(cudaMemcpy2DAsync(r64, L * sizeof(double2), B, ldb * sizeof(double2),
+                                            N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+            } else {
+                VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
+                                            N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+                apply64(e64, Ax);
+                ++mv64;
+                k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, r64, L);
+                VSIE_CUDA(cudaGetLastError());
+            }
             VSIE_CUDA(cudaMemcpyAsync(w64, r64, pN * sizeof(double2), cudaMemcpyDeviceToDevice, st));
             std::vector<double> rn2;
             K64.norms(rn2);
@@ -584,6 +590,7 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
                 if (!std::isfinite(relres[q])) throw Error(VSIE_EBREAKDOWN, "non-finite residual");
                 conv = conv && relres[q] <= tol;
             }
+            have_res = true;   // relres is the true FP64 residual of the current x
             if (conv) break;
             // inner correction to inner_tol (never tighter than the outer target needs)
             double itol = inner_tol;
@@ -612,22 +619,24 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             }
             k_add_widen<<<nblk(N * p), 256, 0, st>>>(corr, L, N, p, X, ldx);
             VSIE_CUDA(cudaGetLastError());
+            have_res = false;
         }
     }
-    // final true FP64 residual
-    VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
-                                N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
-    apply64(e64, Ax);
-    ++mv64;
-    k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, w64, L);
-    VSIE_CUDA(cudaGetLastError());
-    std::vector<double> rn2;
-    K64.norms(rn2);
-    bool conv = true;
-    for (int q = 0; q < p; ++q) {
-        relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
-        conv = conv && relres[q] <= tol;
+    // final true FP64 residual (already at hand when the refinement loop stopped
+    // right after computing it)
+    if (!have_res) {
+        VSIE_CUDA(cudaMemcpy2DAsync(e64, L * sizeof(double2), X, ldx * sizeof(double2),
+                                    N * sizeof(double2), p, cudaMemcpyDeviceToDevice, st));
+        apply64(e64, Ax);
+        ++mv64;
+        k_sub<double><<<nblk(N * p), 256, 0, st>>>(B, ldb, Ax, L, N, p, w64, L);
+        VSIE_CUDA(cudaGetLastError());
+        std::vector<double> rn2;
+        K64.norms(rn2);
+        for (int q = 0; q < p; ++q) relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
     }
+    bool conv = true;
+    for (int q = 0; q < p; ++q) conv = conv && relres[q] <= tol;
     VSIE_CUDA(cudaStreamSynchronize(st));
     if (info) {
         *info = vsie_solve_info{};

@@ -936,6 +936,11 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             for (int q = 0; q < 4; ++q) P.tt_core[a][q] = reinterpret_cast<const double*>(B.tt[a][q].data());
         }
     }
+#ifdef VSIE_TRACE
+    fprintf(stderr, "[vsie setup] m_f %d m_n %d aca rank %d tt ranks %d,%d,%d | %d,%d,%d | %d,%d,%d\n", m_f, m_n,
+            P.aca_rank, P.tt_rank[0][0], P.tt_rank[0][1], P.tt_rank[0][2], P.tt_rank[1][0], P.tt_rank[1][1],
+            P.tt_rank[1][2], P.tt_rank[2][0], P.tt_rank[2][1], P.tt_rank[2][2]);
+#endif
     vsie_options fo = o;
     fo.stencil = s;
     Ctx* c = nullptr;

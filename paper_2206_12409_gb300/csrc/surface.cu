@@ -78,6 +78,77 @@ __global__ void k_spmv_add(int64_t nr, int p, const int32_t* __restrict__ rows,
 
 static inline int nblk(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+// First TT core against the body (Eq. (mvp), last step, and Eq. (tmvp), first
+// step), all p right-hand sides, material voxels only.  G1 is n1 x r1
+// (column-major), a body column is the n1 voxels i1 of one (i2, i3).
+constexpr int kG1Cols = 8;    // columns per CTA, forward
+constexpr int kG1tCols = 32;  // columns per CTA, transposed
+
+// y[j][i1 + n1 col] += sum_r G1[i1 + n1 r] t3[j][r + r1 col]   (mask[i1 + n1 col] != 0)
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_tt_g1(const cx<R>* __restrict__ G1, int n1, int r1, int ncol, const cx<R>* __restrict__ t3, int64_t st3,
+        const uint8_t* __restrict__ mask, cx<R>* __restrict__ Y, int64_t ldy) {
+    extern __shared__ __align__(16) unsigned char g1_smem[];
+    cx<R>* g = reinterpret_cast<cx<R>*>(g1_smem);
+    for (int i = threadIdx.x; i < n1 * r1; i += blockDim.x) g[i] = G1[i];
+    __syncthreads();
+    const int j = blockIdx.y, col0 = blockIdx.x * kG1Cols;
+    const cx<R>* t = t3 + (size_t)j * st3;
+    cx<R>* y = Y + (size_t)j * ldy;
+    for (int e = threadIdx.x; e < n1 * kG1Cols; e += blockDim.x) {
+        const int i1 = e % n1, col = col0 + e / n1;
+        if (col >= ncol) break;
+        const size_t v = (size_t)i1 + (size_t)n1 * col;
+        if (!mask[v]) continue;
+        cx<R> acc = mk<cx<R>>(0, 0);
+        const cx<R>* tc = t + (size_t)r1 * col;
+        for (int r = 0; r < r1; ++r) cfma(acc, g[i1 + n1 * r], tc[r]);
+        y[v] = cadd(y[v], acc);
+    }
+}
+
+// z[j][r + r1 col] = sum_i1 G1[i1 + n1 r] x[j][i1 + n1 col]   (x read as 0 where mask == 0)
+// shared memory: G1 transposed with row stride n1 + 1, then the x columns with
+// stride n1 + 1 (conflict-free reads across r and across columns)
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_tt_g1t(const cx<R>* __restrict__ G1, int n1, int r1, int ncol, const cx<R>* __restrict__ X, int64_t ldx,
+         const uint8_t* __restrict__ mask, cx<R>* __restrict__ Z, int64_t sz) {
+    extern __shared__ __align__(16) unsigned char g1_smem[];
+    cx<R>* gt = reinterpret_cast<cx<R>*>(g1_smem);          // r1 x (n1 + 1)
+    cx<R>* xs = gt + (size_t)r1 * (n1 + 1);                  // kG1tCols x (n1 + 1)
+    const int j = blockIdx.y, col0 = blockIdx.x * kG1tCols;
+    for (int i = threadIdx.x; i < n1 * r1; i += blockDim.x) {
+        const int i1 = i % n1, r = i / n1;
+        gt[r * (n1 + 1) + i1] = G1[i];
+    }
+    const cx<R>* x = X + (size_t)j * ldx;
+    for (int e = threadIdx.x; e < n1 * kG1tCols; e += blockDim.x) {
+        const int i1 = e % n1, c = e / n1, col = col0 + c;
+        cx<R> v = mk<cx<R>>(0, 0);
+        if (col < ncol) {
+            const size_t q = (size_t)i1 + (size_t)n1 * col;
+            if (mask[q]) v = x[q];
+        }
+        xs[c * (n1 + 1) + i1] = v;
+    }
+    __syncthreads();
+    cx<R>* z = Z + (size_t)j * sz;
+    for (int e = threadIdx.x; e < r1 * kG1tCols; e += blockDim.x) {
+        const int r = e % r1, c = e / r1, col = col0 + c;
+        if (col >= ncol) break;
+        cx<R> acc = mk<cx<R>>(0, 0);
+        const cx<R>* gr = gt + (size_t)r * (n1 + 1);
+        const cx<R>* xc = xs + (size_t)c * (n1 + 1);
+        for (int i1 = 0; i1 < n1; ++i1) cfma(acc, gr[i1], xc[i1]);
+        z[(size_t)r + (size_t)r1 * col] = acc;
+    }
+}
+
+template <typename R>
+static size_t g1t_smem(int n1, int r1) { return ((size_t)r1 + kG1tCols) * (n1 + 1) * sizeof(cx<R>); }
+
 template <typename R>
 void surface_pre(Ctx& c, int p, const cx<R>* X, int64_t ldx, cudaStream_t st) {
     OpData<R>& d = data<R>(c);
@@ -159,11 +230,34 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
                      d.t2, (int64_t)r2 * n3, 0, 1, nullptr, nullptr, st);
             cgemm<R>(c, OP_N, r1 * n2, n3 * p, r2, one, G[1], (int64_t)r1 * n2, 0, d.t2, r2, 0,
                      zero, d.t3, (int64_t)r1 * n2, 0, 1, nullptr, nullptr, st);
-            cgemm<R>(c, OP_N, n1, n2 * n3, r1, one, G[0], n1, 0, d.t3, r1,
-                     (int64_t)r1 * n2 * n3, one, Y + boff, n1, ldy, p, nullptr, c.mask, st);
+            const int ncol = n2 * n3;
+            const size_t sm1 = (size_t)n1 * r1 * sizeof(C), sm2 = g1t_smem<R>(n1, r1);
+            const bool fused = sm1 <= 200 * 1024 && sm2 <= 200 * 1024;
+            if (fused && (sm1 > 48 * 1024 || sm2 > 48 * 1024)) {
+                VSIE_CUDA(cudaFuncSetAttribute(k_tt_g1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sm1));
+                VSIE_CUDA(cudaFuncSetAttribute(k_tt_g1t<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sm2));
+            }
+            if (fused) {
+                k_tt_g1<R><<<dim3((ncol + kG1Cols - 1) / kG1Cols, p), 256, sm1, st>>>(
+                    G[0], n1, r1, ncol, d.t3, (int64_t)r1 * ncol, c.mask, Y + boff, ldy);
+                VSIE_CUDA(cudaGetLastError());
+                prof_count(c, 1);
+            } else {
+                cgemm<R>(c, OP_N, n1, n2 * n3, r1, one, G[0], n1, 0, d.t3, r1,
+                         (int64_t)r1 * n2 * n3, one, Y + boff, n1, ldy, p, nullptr, c.mask, st);
+            }
             // Eq. (tmvp): Z1 = G1^T (M x_b); Z2 = G2^T Z1; Z3 = G3^T Z2; y_f += G4^T Z3
-            cgemm<R>(c, OP_T, r1, n2 * n3, n1, one, G[0], n1, 0, X + boff, n1, ldx, zero, d.t3,
-                     r1, (int64_t)r1 * n2 * n3, p, c.mask, nullptr, st);
+            if (fused) {
+                k_tt_g1t<R><<<dim3((ncol + kG1tCols - 1) / kG1tCols, p), 256, sm2, st>>>(
+                    G[0], n1, r1, ncol, X + boff, ldx, c.mask, d.t3, (int64_t)r1 * ncol);
+                VSIE_CUDA(cudaGetLastError());
+                prof_count(c, 1);
+            } else {
+                cgemm<R>(c, OP_T, r1, n2 * n3, n1, one, G[0], n1, 0, X + boff, n1, ldx, zero, d.t3,
+                         r1, (int64_t)r1 * n2 * n3, p, c.mask, nullptr, st);
+            }
             cgemm<R>(c, OP_T, r2, n3 * p, r1 * n2, one, G[1], (int64_t)r1 * n2, 0, d.t3,
                      (int64_t)r1 * n2, 0, zero, d.t2, r2, 0, 1, nullptr, nullptr, st);
             cgemm<R>(c, OP_T, r3, p, r2 * n3, one, G[2], (int64_t)r2 * n3, 0, d.t2,

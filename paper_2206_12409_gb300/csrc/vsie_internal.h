@@ -132,7 +132,7 @@ struct OpData {
 // Per-context profiling: kernel groups, launch counts (always), CUDA-event time
 // and algorithmic bytes (when enabled by vsie_profile).
 enum ProfGroup { PG_FFTCONV = 0, PG_PFFT = 1, PG_PRECORR = 2, PG_SURF = 3, PG_TT = 4, PG_KRYLOV = 5,
-                 PG_PRECOND = 6, PG_N = 7 };
+                 PG_PRECOND = 6, PG_FFTCONV64 = 7, PG_N = 8 };
 struct Prof {
     bool on = false;
     int group = PG_SURF;                       // group charged by nested launchers

@@ -31,7 +31,7 @@ EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie
            "vsie_net_attach", "vsie_precond_apply", "vsie_net_last_error", "vsie_net_destroy",
            "vsie_destroy"]
 PROFILE_GROUPS = {"fft_conv": 0, "pfft": 1, "precorrection": 2, "surface": 3, "tt": 4,
-                  "krylov": 5, "precond": 6}
+                  "krylov": 5, "precond": 6, "fft_conv_c128": 7}
 
 
 class VsieError(RuntimeError):
