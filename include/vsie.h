@@ -243,8 +243,12 @@ VSIE_API vsie_status vsie_volume_matvec_static(vsie_ctx* ctx, int32_t p, const v
                                                vsie_stream stream);
 
 /* Persistence of a context's operator (Sec. VI: compressed coupling matrices
- * stored and reused).  Not implemented: both return VSIE_EUNSUPPORTED; set-up
- * is deterministic and is re-run instead. */
+ * stored and reused).  vsie_save writes the body grid, materials, frequency,
+ * options, every part of vsie_parts (the far block copied from the device) and
+ * the port table to a versioned binary file at `path`; vsie_load reads it back,
+ * checks every array size against the header, and recreates the context with
+ * vsie_create (set-up integrals are not recomputed).  EINVAL for unreadable,
+ * foreign or truncated files; the caller owns the new context. */
 VSIE_API vsie_status vsie_save(const vsie_ctx* ctx, const char* path);
 VSIE_API vsie_status vsie_load(const char* path, vsie_ctx** out);
 
