@@ -12,8 +12,10 @@
 // Tensors are FP32, channel-major (C, D, H, W) with W fastest.  Weights are kept
 // as FP32 master copies (updated by Adam) and used by the kernels as BF16
 // copies in two layouts (forward: [ci][tap][co]; data gradient: the same
-// kernel run with [co][flipped tap][ci]).  Every sum accumulates in FP32; the
-// weight and bias gradients reduce over voxel chunks in a fixed order.
+// kernel run with [co][flipped tap][ci]).  The 3x3x3 convolutions run on the
+// tensor cores (k_conv3_mma), the 1x1x1 head and the weight gradient on the
+// FP32 pipes.  Every sum accumulates in FP32; the weight and bias gradients
+// reduce over voxel chunks in a fixed order.
 // Skip tensors are written by the encoder straight into the channel slice of
 // the decoder's concatenation buffer, so no concatenation copies exist.
 #include "vsie_internal.h"
@@ -112,6 +114,111 @@ k_conv(const float* __restrict__ x, int Ci, int D, int H, int W, const __nv_bflo
         float r = acc[c] + (bias ? bias[co] : 0.f);
         if (relu) r = fmaxf(r, 0.f);
         y[(size_t)co * V + v] = r;
+    }
+}
+
+// Tensor-core form of the 3x3x3 convolution (implicit GEMM on mma.sync
+// m16n8k16, BF16 operands, FP32 accumulation):
+//   y[co][v] = bias[co] + sum_{ci, tap} w[ci][tap][co] x[ci][v + tap - 1],
+// M = 16 output channels per CTA (blockIdx.z), N = an 8 x 8 x 4 voxel tile
+// (blockIdx.x over x-y tiles, blockIdx.y over z), K = 16 input channels x 27 taps
+// per staged chunk.  The activations are split into two BF16 terms,
+// x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), and both are multiplied by the
+// BF16 weights, so the products keep about 16 bits of the FP32 activations.
+// Warp w owns z-slice w of the tile: 8 rows of 8 voxels = 8 n-tiles.
+// Shared memory (dynamic): input hi and lo as [position][16 channels + pad] and
+// the weights as [tap][16 co][16 ci + pad], padded so that the fragment loads
+// of a warp fall in distinct banks.
+constexpr int MC_PAD = 24;                    // BF16 per staged row (16 used)
+constexpr int MC_SX = TX + 2, MC_SY = TY + 2, MC_SZ = TZ + 2, MC_SV = MC_SX * MC_SY * MC_SZ;
+constexpr size_t kConvMmaSmem = (size_t)(2 * MC_SV + 27 * 16) * MC_PAD * sizeof(__nv_bfloat16);
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128)
+k_conv3_mma(const float* __restrict__ x, int Ci, int D, int H, int W, const __nv_bfloat16* __restrict__ wt,
+            const float* __restrict__ bias, int Co, int relu, float* __restrict__ y) {
+    extern __shared__ __align__(16) unsigned char mc_smem[];
+    __nv_bfloat16* s_hi = reinterpret_cast<__nv_bfloat16*>(mc_smem);
+    __nv_bfloat16* s_lo = s_hi + MC_SV * MC_PAD;
+    __nv_bfloat16* s_w = s_lo + MC_SV * MC_PAD;          // [27][16 co][MC_PAD]
+    const int tiles_x = (W + TX - 1) / TX;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    const int z0 = blockIdx.y * TZ, co0 = blockIdx.z * 16;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const size_t V = (size_t)D * H * W;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+    for (int cb = 0; cb < Ci; cb += 16) {
+        __syncthreads();
+        // input halo tile, 16 channels, split into hi and lo
+        for (int e = t; e < 16 * MC_SV; e += blockDim.x) {
+            const int c = e / MC_SV, r = e - c * MC_SV;
+            const int sx = r % MC_SX, sy = (r / MC_SX) % MC_SY, sz = r / (MC_SX * MC_SY);
+            const int gx = x0 + sx - 1, gy = y0 + sy - 1, gz = z0 + sz - 1;
+            float v = 0.f;
+            if (cb + c < Ci && gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
+                v = x[(size_t)(cb + c) * V + ((size_t)gz * H + gy) * W + gx];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            s_hi[r * MC_PAD + c] = hi;
+            s_lo[r * MC_PAD + c] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        // weights of this chunk: s_w[tap][o][c] = wt[cb + c][tap][co0 + o]
+        for (int e = t; e < 27 * 16 * 16; e += blockDim.x) {
+            const int o = e % 16, c = (e / 16) % 16, tap = e / 256;
+            __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+            if (cb + c < Ci && co0 + o < Co) v = wt[((size_t)(cb + c) * 27 + tap) * Co + co0 + o];
+            s_w[(tap * 16 + o) * MC_PAD + c] = v;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            const __nv_bfloat16* wa = s_w + (size_t)tap * 16 * MC_PAD;
+            uint32_t a[4];
+            a[0] = *reinterpret_cast<const uint32_t*>(wa + g * MC_PAD + t4 * 2);
+            a[1] = *reinterpret_cast<const uint32_t*>(wa + (g + 8) * MC_PAD + t4 * 2);
+            a[2] = *reinterpret_cast<const uint32_t*>(wa + g * MC_PAD + t4 * 2 + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(wa + (g + 8) * MC_PAD + t4 * 2 + 8);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                // n-tile j: the row of 8 voxels (x = 0..7) at y = j, z = warp
+                const int pos = ((warp + dz) * MC_SY + (j + dy)) * MC_SX + (g + dx);
+                const __nv_bfloat16* bh = s_hi + pos * MC_PAD + t4 * 2;
+                const __nv_bfloat16* bl = s_lo + pos * MC_PAD + t4 * 2;
+                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t*>(bh),
+                         *reinterpret_cast<const uint32_t*>(bh + 8));
+                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t*>(bl),
+                         *reinterpret_cast<const uint32_t*>(bl + 8));
+            }
+        }
+    }
+    // C fragment: rows g, g + 8 (output channel), columns 2 t4, 2 t4 + 1 (voxel x)
+    const int gz = z0 + warp;
+    if (gz >= D) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int gy = y0 + j;
+        if (gy >= H) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int co = co0 + g + (q >= 2 ? 8 : 0);
+            const int gx = x0 + t4 * 2 + (q & 1);
+            if (co >= Co || gx >= W) continue;
+            float r = acc[j][q] + (bias ? bias[co] : 0.f);
+            if (relu) r = fmaxf(r, 0.f);
+            y[(size_t)co * V + ((size_t)gz * H + gy) * W + gx] = r;
+        }
     }
 }
 
@@ -426,22 +533,29 @@ struct Net {
     }
     static constexpr int kChunks = 32;
 
+    static void conv3_mma(const float* x, int ci, int d, int h, int ww, const __nv_bfloat16* w,
+                          const float* bias, int co, bool relu, float* y, cudaStream_t st) {
+        dim3 g(((ww + TX - 1) / TX) * ((h + TY - 1) / TY), (d + TZ - 1) / TZ, (co + 15) / 16);
+        k_conv3_mma<<<g, 128, kConvMmaSmem, st>>>(x, ci, d, h, ww, w, bias, co, relu ? 1 : 0, y);
+    }
     void conv(int l, const float* x, int d, int h, int ww, float* y, bool relu, cudaStream_t st) {
         const LayerDef& L = kLayers[l];
+        if (L.k == 3) {
+            conv3_mma(x, L.ci, d, h, ww, wf[l], b[l], L.co, relu, y, st);
+            return;
+        }
         dim3 g(((ww + TX - 1) / TX) * ((h + TY - 1) / TY), (d + TZ - 1) / TZ, (L.co + COT - 1) / COT);
-        if (L.k == 3)
-            k_conv<3><<<g, 256, 0, st>>>(x, L.ci, d, h, ww, wf[l], b[l], L.co, relu ? 1 : 0, y);
-        else
-            k_conv<1><<<g, 256, 0, st>>>(x, L.ci, d, h, ww, wf[l], b[l], L.co, relu ? 1 : 0, y);
+        k_conv<1><<<g, 256, 0, st>>>(x, L.ci, d, h, ww, wf[l], b[l], L.co, relu ? 1 : 0, y);
     }
     // gradient wrt the layer input: a convolution with the flipped, transposed weights
     void conv_dx(int l, const float* gz, int d, int h, int ww, float* gx, cudaStream_t st) {
         const LayerDef& L = kLayers[l];
+        if (L.k == 3) {
+            conv3_mma(gz, L.co, d, h, ww, wb[l], nullptr, L.ci, false, gx, st);
+            return;
+        }
         dim3 g(((ww + TX - 1) / TX) * ((h + TY - 1) / TY), (d + TZ - 1) / TZ, (L.ci + COT - 1) / COT);
-        if (L.k == 3)
-            k_conv<3><<<g, 256, 0, st>>>(gz, L.co, d, h, ww, wb[l], nullptr, L.ci, 0, gx);
-        else
-            k_conv<1><<<g, 256, 0, st>>>(gz, L.co, d, h, ww, wb[l], nullptr, L.ci, 0, gx);
+        k_conv<1><<<g, 256, 0, st>>>(gz, L.co, d, h, ww, wb[l], nullptr, L.ci, 0, gx);
     }
     void conv_dw(int l, const float* x, const float* gz, int d, int h, int ww, cudaStream_t st) {
         const LayerDef& L = kLayers[l];
@@ -610,6 +724,8 @@ vsie_status vsie_net_create(uint64_t seed, vsie_net** out) {
     try {
         n = new Net();
         n->alloc_params();
+        VSIE_CUDA(cudaFuncSetAttribute(k_conv3_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kConvMmaSmem));
         // He-normal initial weights, zero biases
         std::mt19937_64 rng(seed);
         std::normal_distribution<float> nd(0.f, 1.f);
