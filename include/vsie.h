@@ -209,6 +209,20 @@ VSIE_API vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t
                        int64_t ldx, double tol, const vsie_solve_opts* opts,
                        vsie_solve_info* info, vsie_stream stream);
 
+/* Uneven batch (many independent problems of different sizes): solve
+ * ctxs[i] Z_i X_i = B_i (p[i] columns, leading dimensions ldb[i], ldx[i], device
+ * double2) for i < nctx with the options and tolerance of vsie_solve.  Up to
+ * nthreads host threads (0: 8) each take the next context and solve it on a
+ * stream of their own, so the kernels of small problems overlap on the GPU.
+ * Every context may appear once, and with precond = 2 no two contexts may share
+ * a network (EINVAL).  info and status (nctx entries each, host)
+ * may be NULL; returns VSIE_OK when every solve did, else the first failing
+ * status.  Synchronous. */
+VSIE_API vsie_status vsie_solve_batch(int32_t nctx, vsie_ctx* const* ctxs, const int32_t* p,
+                                      const void* const* B, const int64_t* ldb, void* const* X,
+                                      const int64_t* ldx, double tol, const vsie_solve_opts* opts,
+                                      vsie_solve_info* info, vsie_status* status, int32_t nthreads);
+
 /* Profiling.  vsie_profile(ctx, 1) clears the counters and starts recording a
  * CUDA event pair around every kernel group launched by calls on the context
  * (0 stops recording; launch counts are always kept).  vsie_profile_query

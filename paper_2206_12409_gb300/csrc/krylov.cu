@@ -19,7 +19,9 @@
 #include "vsie_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <complex>
 
@@ -680,6 +682,66 @@ vsie_status vsie_solve(vsie_ctx* ctx, int32_t p, const void* B, int64_t ldb, voi
         c->err = e.msg;
         return e.st;
     }
+}
+
+vsie_status vsie_solve_batch(int32_t nctx, vsie_ctx* const* ctxs, const int32_t* p, const void* const* B,
+                             const int64_t* ldb, void* const* X, const int64_t* ldx, double tol,
+                             const vsie_solve_opts* opts, vsie_solve_info* info, vsie_status* status,
+                             int32_t nthreads) {
+    if (nctx < 0 || (nctx > 0 && (!ctxs || !p || !B || !ldb || !X || !ldx))) {
+        set_global_err("null batch arrays or nctx < 0");
+        return VSIE_EINVAL;
+    }
+    if (nctx == 0) return VSIE_OK;
+    const bool learned = opts && opts->precond == 2;
+    for (int i = 0; i < nctx; ++i)
+        for (int k = 0; k < i; ++k) {
+            if (ctxs[i] == ctxs[k]) {   // a context is not thread-safe
+                set_global_err("a context appears twice in the batch");
+                return VSIE_EINVAL;
+            }
+            if (learned && ctxs[i] && ctxs[k] && reinterpret_cast<Ctx*>(ctxs[i])->net &&
+                reinterpret_cast<Ctx*>(ctxs[i])->net == reinterpret_cast<Ctx*>(ctxs[k])->net) {
+                set_global_err("contexts of a batch share one network (its buffers are not thread-safe)");
+                return VSIE_EINVAL;
+            }
+        }
+    std::vector<vsie_status> st(nctx, VSIE_OK);
+    const int nw = std::max(1, std::min<int>(nthreads > 0 ? nthreads : 8, nctx));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        cudaStream_t s = nullptr;
+        int have_dev = -1;
+        for (int i = next++; i < nctx; i = next++) {
+            if (!ctxs[i]) { st[i] = VSIE_EINVAL; continue; }
+            const int dev = reinterpret_cast<Ctx*>(ctxs[i])->device;
+            if (dev != have_dev) {
+                if (s) cudaStreamDestroy(s);
+                s = nullptr;
+                if (cudaSetDevice(dev) != cudaSuccess ||
+                    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                    cudaGetLastError();
+                    st[i] = VSIE_ECUDA;
+                    have_dev = -1;
+                    continue;
+                }
+                have_dev = dev;
+            }
+            st[i] = vsie_solve(ctxs[i], p[i], B[i], ldb[i], X[i], ldx[i], tol, opts, info ? &info[i] : nullptr,
+                               reinterpret_cast<vsie_stream>(s));
+        }
+        if (s) cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    vsie_status first = VSIE_OK;
+    for (int i = 0; i < nctx; ++i) {
+        if (status) status[i] = st[i];
+        if (first == VSIE_OK && st[i] != VSIE_OK) first = st[i];
+    }
+    return first;
 }
 
 vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t* ports, double V, void* B,

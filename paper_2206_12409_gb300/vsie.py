@@ -29,7 +29,7 @@ EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie
            "vsie_net_create", "vsie_net_num_params", "vsie_net_set_params", "vsie_net_get_params",
            "vsie_net_forward", "vsie_net_backward", "vsie_net_step", "vsie_net_train",
            "vsie_net_attach", "vsie_precond_apply", "vsie_net_last_error", "vsie_net_destroy",
-           "vsie_destroy"]
+           "vsie_solve_batch", "vsie_destroy"]
 PROFILE_GROUPS = {"fft_conv": 0, "pfft": 1, "precorrection": 2, "surface": 3, "tt": 4,
                   "krylov": 5, "precond": 6, "fft_conv_c128": 7}
 
@@ -142,6 +142,11 @@ def load_library(path: str | None = None):
                                   C.POINTER(C.c_double), P]
     lib.vsie_net_train.restype = C.c_int
     lib.vsie_net_train.argtypes = [P, P, C.c_int32, C.c_double, C.c_uint64, F, P]
+    lib.vsie_solve_batch.restype = C.c_int
+    lib.vsie_solve_batch.argtypes = [C.c_int32, C.POINTER(P), C.POINTER(C.c_int32), C.POINTER(P),
+                                     C.POINTER(C.c_int64), C.POINTER(P), C.POINTER(C.c_int64), C.c_double,
+                                     C.POINTER(vsie_solve_opts), C.POINTER(vsie_solve_info),
+                                     C.POINTER(C.c_int), C.c_int32]
     lib.vsie_precond_apply.restype = C.c_int
     lib.vsie_precond_apply.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
     lib.vsie_net_attach.restype = C.c_int
@@ -488,3 +493,21 @@ def vsie_precond_apply(ctx, p, X, ldx, Y, ldy, kind, stream=0):
     """Y = M X with the FP32 preconditioner (kind 0 block, 2 learned)."""
     _check(load_library().vsie_precond_apply(ctx, int(p), C.c_void_p(int(X)), int(ldx), C.c_void_p(int(Y)),
                                              int(ldy), int(kind), C.c_void_p(int(stream))), ctx)
+
+
+def vsie_solve_batch(ctxs, p, B, ldb, X, ldx, tol, opts=None, nthreads=0):
+    """Concurrent solves of independent contexts; returns (status, statuses, infos)."""
+    n = len(ctxs)
+    lib = load_library()
+    P = C.c_void_p
+    ca = (P * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    pa = (C.c_int32 * n)(*[int(v) for v in p])
+    ba = (P * n)(*[int(v) for v in B])
+    xa = (P * n)(*[int(v) for v in X])
+    lb = (C.c_int64 * n)(*[int(v) for v in ldb])
+    lx = (C.c_int64 * n)(*[int(v) for v in ldx])
+    infos = (vsie_solve_info * n)()
+    sts = (C.c_int * n)()
+    st = lib.vsie_solve_batch(n, ca, pa, ba, lb, xa, lx, float(tol),
+                              C.byref(opts) if opts is not None else None, infos, sts, int(nthreads))
+    return st, list(sts), list(infos)
