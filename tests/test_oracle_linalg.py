@@ -89,3 +89,36 @@ def test_gmres_estimate_equals_true_residual_nonnormal_complex():
         xk, ik = gmres.gmres(lambda v: A @ v, b, 1e-30, restart=k, maxit=k)
         true = np.linalg.norm(A @ xk - b) / np.linalg.norm(b)
         assert abs(ik["est"] - true) <= 1e-9 * true
+
+
+def test_fgmres_with_a_changing_preconditioner():
+    """Flexible GMRES (Saad 1993) keeps z_j = M_j(v_j): with a preconditioner that
+    changes at every call it still converges to the LU solution, and its
+    unrestarted residual after k steps is the minimum over x0 + span(z_0..z_k-1)
+    (checked by a direct least-squares solve over the same directions)."""
+    rng = np.random.default_rng(5)
+    n = 60
+    A = 2 * np.eye(n) + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    xs = np.linalg.solve(A, b)
+    Mi = np.linalg.inv(A)
+    calls = []
+
+    def M(v):   # a different, noisy approximate inverse at every call
+        k = len(calls)
+        E = np.random.default_rng(100 + k).standard_normal((n, n)) * 0.05 / np.sqrt(n)
+        z = (Mi + E) @ v
+        calls.append(z.copy())
+        return z
+
+    x, info = gmres.gmres(lambda v: A @ v, b, 1e-10, restart=20, M=M)
+    assert info["relres"] <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+    # minimal-residual property of one cycle of k steps
+    calls.clear()
+    k = 6
+    xk, ik = gmres.gmres(lambda v: A @ v, b, 1e-30, restart=k, maxit=k, M=M)
+    Z = np.array(calls[:k]).T                          # the k directions used
+    y, *_ = np.linalg.lstsq(A @ Z, b, rcond=None)
+    best = np.linalg.norm(A @ (Z @ y) - b)
+    assert abs(np.linalg.norm(A @ xk - b) - best) <= 1e-10 * np.linalg.norm(b)
