@@ -186,3 +186,42 @@ def adam_step(P, G, M, V, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         mh = M[k] / (1 - b1 ** t)
         vh = V[k] / (1 - b2 ** t)
         P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def apply_preconditioner(P, grid, eps_r, sigma, freq_hz, v_body):
+    """The learned right preconditioner on the body block (the application step of
+    the network inside flexible GMRES), for one body vector v (component-major,
+    3 n_v complex):
+        u = D^-1 v    with D the diagonal of Z_bb: h^3 (1/chi - T(0)) on material
+                      voxels, 1 on vacuum voxels (identity rows),
+        s = RMS(u)    over all 3 n_v entries,
+        y = net([Re u_a / s, Im u_a / s (a = x, y, z); (eps_r - 1) / 50; sigma])
+                      on the grid padded to multiples of 8 (zeros outside),
+        z_a = u_a + s (y_2a + i y_2a+1)   on material voxels,  z_a = u_a  on vacuum.
+    Pinned through unet.forward (see the tests of this module) and the definition
+    of the body diagonal in volume.dense_Zbb."""
+    from . import physics
+    n1, n2, n3 = grid.n
+    nv = n1 * n2 * n3
+    chi = physics.chi(eps_r, sigma, freq_hz)
+    _, k0 = physics.omega_k0(freq_hz)
+    mat = chi != 0
+    d = np.ones(nv, np.complex128)
+    d[mat] = 1.0 / (grid.h ** 3 * (1.0 / chi[mat] - physics.self_term(k0, grid.h)))
+    u = np.asarray(v_body, np.complex128).reshape(3, nv) * d[None, :]
+    s = np.sqrt(np.sum(np.abs(u) ** 2) / (3 * nv))
+    pad = lambda n: (n + 7) // 8 * 8
+    D, H, W = pad(n3), pad(n2), pad(n1)
+    x = np.zeros((8, D, H, W))
+    cube = lambda f: f.reshape(n3, n2, n1)          # voxel i1 + n1 (i2 + n2 i3) -> [i3, i2, i1]
+    for a in range(3):
+        x[2 * a, :n3, :n2, :n1] = cube(u[a].real) / s
+        x[2 * a + 1, :n3, :n2, :n1] = cube(u[a].imag) / s
+    x[6, :n3, :n2, :n1] = cube((np.asarray(eps_r, float) - 1.0) / 50.0)
+    x[7, :n3, :n2, :n1] = cube(np.asarray(sigma, float))
+    y, _ = forward(P, x)
+    z = u.copy()
+    for a in range(3):
+        corr = (y[2 * a, :n3, :n2, :n1] + 1j * y[2 * a + 1, :n3, :n2, :n1]).reshape(nv)
+        z[a, mat] += s * corr[mat]
+    return z.reshape(-1)

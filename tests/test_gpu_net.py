@@ -181,3 +181,35 @@ def test_zero_network_equals_block_preconditioner():
     finally:
         V.vsie_destroy(ctx)
         V.vsie_net_destroy(net)
+
+
+def test_learned_preconditioner_application_matches_oracle():
+    """vsie_precond_apply (kind 2) against the oracle's restatement of the
+    preconditioner (Jacobi scaling, RMS normalisation, network, masked
+    correction) on a small head phantom, with the same parameters."""
+    import torch
+    from paper_2206_12409_gb300 import vsie as V
+    from paper_2206_12409_gb300 import inputs as I
+    g, er, sg = I.layered_head_phantom(n=(16, 16, 20), h=1.3e-2, seed=6)
+    prob = I.Problem("h", g, er, sg, 298e6)
+    ctx = V.setup_problem(prob, max_rhs=2)
+    P = _params(21)
+    net = V.vsie_net_create(1)
+    try:
+        V.vsie_net_set_params(net, _pack(P))
+        V.vsie_net_attach(ctx, net)
+        N = V.vsie_sizes(ctx)[0]
+        assert N == 3 * g.nv
+        rng = np.random.default_rng(22)
+        x = (rng.standard_normal((2, N)) + 1j * rng.standard_normal((2, N))).astype(np.complex64)
+        X = torch.from_numpy(x).cuda()
+        Y = torch.zeros_like(X)
+        V.vsie_precond_apply(ctx, 2, X.data_ptr(), N, Y.data_ptr(), N, 2)
+        torch.cuda.synchronize()
+        y = Y.cpu().numpy()
+        for c in range(2):
+            zo = unet.apply_preconditioner(P, g, er, sg, prob.freq_hz, x[c].astype(np.complex128))
+            assert _rel(y[c], zo) < 1e-4
+    finally:
+        V.vsie_destroy(ctx)
+        V.vsie_net_destroy(net)

@@ -101,3 +101,36 @@ def test_adam_first_step_is_signed_lr():
     unet.adam_step(P, G, M, V, 1, lr=0.01)
     ref = np.array([1.0 - 0.01 * 0.3 / (0.3 + 1e-8), -2.0 + 0.01 * 4.0 / (4.0 + 1e-8), 0.5])
     assert np.abs(P["a"] - ref).max() < 1e-15
+
+
+def test_preconditioner_application_pins():
+    """The oracle's learned-preconditioner application: with an all-zero network
+    it is the inverse of the body block's diagonal (taken from the brute-force
+    dense Z_bb) and the identity on vacuum voxels; for any network it is
+    positively homogeneous, M(a v) = a M(v) for a > 0 (the input is normalised
+    by its RMS and the correction rescaled by it)."""
+    from oracle import physics, volume
+    from paper_2206_12409_gb300 import inputs as I
+    g, er, sg = I.sphere_phantom(n=(6, 6, 6), h=8e-3, radius=20e-3, eps_r=30.0, sigma=0.4)
+    f = 298e6
+    chi = physics.chi(er, sg, f)
+    _, k0 = physics.omega_k0(f)
+    Z, idx = volume.dense_Zbb(g, chi, k0)
+    m = idx.size
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(3 * g.nv) + 1j * rng.standard_normal(3 * g.nv)
+    P0 = {k: 0 * w for k, w in unet.init_params(0).items()}
+    z0 = unet.apply_preconditioner(P0, g, er, sg, f, v).reshape(3, g.nv)
+    vv = v.reshape(3, g.nv)
+    vac = chi == 0
+    assert np.allclose(z0[:, vac], vv[:, vac], rtol=0, atol=1e-15)
+    for a in range(3):
+        diag = np.diag(Z)[a * m:(a + 1) * m]
+        assert np.allclose(z0[a, idx], vv[a, idx] / diag, rtol=1e-12, atol=0)
+    P = unet.init_params(3)
+    z1 = unet.apply_preconditioner(P, g, er, sg, f, v)
+    z2 = unet.apply_preconditioner(P, g, er, sg, f, 7.5 * v)
+    assert np.linalg.norm(z2 - 7.5 * z1) <= 1e-12 * np.linalg.norm(z2)
+    # the network's correction is present on material voxels only
+    assert np.linalg.norm((z1.reshape(3, g.nv) - z0)[:, vac]) == 0.0
+    assert np.linalg.norm((z1.reshape(3, g.nv) - z0)[:, ~vac]) > 0.0
