@@ -87,3 +87,27 @@ def test_matvec_vs_oracle_hybrid_and_dense(setup_ctx, sphere_loop_shield, hybrid
     Z, idx = dense_reference
     yd = hybrid.dense_matvec(sphere_loop_shield, Z, idx, x)
     assert np.linalg.norm(y - yd) <= 2e-3 * np.linalg.norm(yd)
+
+
+@pytest.mark.parametrize("p", [5, 20])
+def test_multi_rhs_matvec_equals_single_rhs(sphere_loop_shield, p):
+    """A p-column matvec (p above the 16-column width of the tall-skinny and
+    panel kernels takes their chunked and generic paths) equals p one-column
+    matvecs, in FP64 and FP32."""
+    import torch
+    from paper_2206_12409_gb300 import vsie as V
+    ctx = V.setup_problem(sphere_loop_shield, max_rhs=p)
+    try:
+        N = V.vsie_sizes(ctx)[0]
+        x = I.random_vectors(N, p).T.copy()
+        for prec, dt, tol in ((V.VSIE_C128, torch.complex128, 1e-13), (V.VSIE_C64, torch.complex64, 1e-5)):
+            X = torch.from_numpy(x).to(dt).cuda()
+            Y = torch.empty_like(X)
+            V.vsie_matvec(ctx, p, X.data_ptr(), N, Y.data_ptr(), N, prec)
+            Y1 = torch.empty_like(X)
+            for j in range(p):
+                V.vsie_matvec(ctx, 1, X[j].data_ptr(), N, Y1[j].data_ptr(), N, prec)
+            torch.cuda.synchronize()
+            assert (torch.linalg.norm(Y - Y1) / torch.linalg.norm(Y1)).item() < tol
+    finally:
+        V.vsie_destroy(ctx)
