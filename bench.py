@@ -346,7 +346,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 operator inside, c128 residual/Gram-Schmidt/Givens",
+            "dtype": "c64 inner operator, basis and Gram-Schmidt; c128 outer residual and Givens",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": world * p, "rhs_per_gpu": p,
                        "N_unknowns": N, "parallelism": "replicas" if world > 1 else "single GPU",
