@@ -1,7 +1,12 @@
 // Complex GEMM used by the surface blocks (K6: Z_ff, Znn, U V^H and conj(V) U^T)
 // and the TT chain (K5: Eq. mvp and Eq. tmvp are sequences of small-K
 // contractions).  Column-major; C_b = alpha op(A_b) B_b + beta C_b.
-// Tiles of BM x BN outputs, BK = 16 staged through shared memory; split-K
+// cgemm2 picks the kernel by shape:
+//   k_gemm_ip     op(A) in {T, H}, few columns of A, long K (inner products);
+//   k_gemm_ts     op(A) in {N, R}, many rows, N <= 16 (one thread per row);
+//   k_cgemm       everything else: tiles of BM x BN outputs, BK = 16 staged
+//                 through shared memory;
+// and gemm_panel applies the FP32 far block stored in row panels.  Split-K
 // partial sums go to a workspace and are reduced in a fixed order (the result
 // does not depend on scheduling).  Optional masks: maskB zeroes B elements,
 // maskC leaves masked C elements untouched.

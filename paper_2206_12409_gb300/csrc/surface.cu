@@ -5,7 +5,10 @@
 //   K4  precorrection y_b += Pre x_n and y_n += Pre^T (M x_b) (two CSR forms);
 //   K6  y_n += Znn x_n + U (V^H x_f),  y_f = Z_ff x_f + conj(V) (U^T x_n);
 //   K5  y_b += M TT(x_f) by Eq. (mvp), y_f += sum_chi TT_chi^T (M x_b,chi) by
-//       Eq. (tmvp), each a chain of contractions (cgemm).
+//       Eq. (tmvp), each a chain of contractions: the first core against the
+//       body by k_tt_g1 / k_tt_g1t (masked, all RHS in one launch), the others
+//       by the GEMM kernels of gemm.cu.
+// The FP32 Z_ff is stored in row panels and applied by gemm_panel.
 #include "vsie_internal.h"
 
 namespace vsie {
