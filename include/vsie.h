@@ -248,10 +248,12 @@ VSIE_API vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms
  * (p * 3 * n3 * (n2 + L2) * L1 complex values, L = FFT lengths of the context)
  * return VSIE_EINVAL.  The first call on a device looks up that array's device
  * address with the device current; make that first call before any stream
- * capture.  All calls on a device share its copy of the array, which keeps the
- * last call's contents; nothing in it needs to start at zero.  Calls that
- * overlap on the same GPU (for example on two streams) race on it.
- * Asynchronous on `stream`. */
+ * capture.  The address is kept for the life of the process, so resetting a
+ * device (cudaDeviceReset) after its first call is not supported.  All calls on
+ * a device share its copy of the array, which keeps the last call's contents;
+ * nothing in it needs to start at zero.  Calls that overlap on the same GPU
+ * (for example on two streams, or solves of vsie_solve_batch running on their
+ * worker threads) race on it.  Asynchronous on `stream`. */
 VSIE_API vsie_status vsie_volume_matvec_static(vsie_ctx* ctx, int32_t p, const void* X, int64_t ldx,
                                                void* Y, int64_t ldy, int32_t precision,
                                                vsie_stream stream);

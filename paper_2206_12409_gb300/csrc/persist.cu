@@ -7,6 +7,7 @@
 // checks against the counts the header implies.
 #include "vsie_internal.h"
 
+#include <cmath>
 #include <cstdio>
 #include <memory>
 
@@ -191,6 +192,15 @@ vsie_status vsie_load(const char* path, vsie_ctx** out) {
         std::vector<int64_t> port_row((size_t)np);
         get(fp, port_row.data(), (size_t)np * sizeof(int64_t));
         const std::vector<double> port_len = get_arr<double>(fp, np);
+        // ports drive surface unknowns only: a row outside [0, m_f + m_n) or a
+        // length that is not a finite positive number would make vsie_rhs_ports
+        // write outside the right-hand side or scale it by garbage
+        for (int64_t q = 0; q < np; ++q) {
+            if (port_row[q] < 0 || port_row[q] >= (int64_t)P.m_f + P.m_n)
+                throw Error(VSIE_EINVAL, "operator file: port row outside the surface unknowns");
+            if (!std::isfinite(port_len[q]) || !(port_len[q] > 0))
+                throw Error(VSIE_EINVAL, "operator file: port edge length must be finite and positive");
+        }
         vsie_ctx* ctx = nullptr;
         const vsie_status st = vsie_create(&g, eps_r.data(), sigma.data(), freq, &o, &P, &ctx);
         if (st != VSIE_OK) return st;
