@@ -196,6 +196,23 @@ VSIE_API vsie_status vsie_matvec(vsie_ctx* ctx, int32_t p, const void* X, int64_
 VSIE_API vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t* ports, double V,
                            void* B, int64_t ldb, vsie_stream stream);
 
+/* Right-hand side of Eq. (hvsie) for an incident plane wave
+ * E_inc(r) = e0 exp(-i k0 khat . r) (Sec. II.A: the equivalent currents are
+ * driven by the incident field; time convention exp(+i omega t)), written to one
+ * column B (device, double2, N values):
+ *   conductor rows  i omega eps0 \int f_m . E_inc dS  (6-point Dunavant rule per
+ *                   triangle; the delta-gap port is the impressed-field case of
+ *                   the same row),
+ *   body rows       i omega eps0 h^3 E_inc(r_p), component-major, on material
+ *                   voxels; 0 on vacuum voxels.
+ * k_hat (host, 3 doubles) is normalised here; e0 (host, 3 doubles, V/m, real
+ * linear polarisation) must be orthogonal to k_hat (EINVAL otherwise).  The
+ * conductor rows need the meshes given to vsie_setup: a context created from
+ * parts or loaded from a file that has conductors returns EUNSUPPORTED.
+ * Asynchronous on `stream`. */
+VSIE_API vsie_status vsie_rhs_planewave(vsie_ctx* ctx, const double k_hat[3], const double e0[3], void* B,
+                                        vsie_stream stream);
+
 /* Solve Z X = B for p right-hand sides to relative FP64 residual tol (Sec. III.A:
  * GMRES with restart; x0 = 0).  B, X: device double2 (C128), column-major N x p.
  * mode 0: every matvec, orthogonalisation and Givens update in FP64.

@@ -374,6 +374,42 @@ __global__ void k_field_points(MeshDev m, int np, const double* __restrict__ pts
     }
 }
 
+// Tested incident plane wave (Sec. II.A; the conductor rows of Eq. (hvsie)):
+// out[m] = scale \int f_m . e0 exp(-i k0 khat . r) dS over both triangles of RWG
+// m, by the 6-point rule.  geo holds, per RWG and per half (T+, then T-), the
+// three vertices, the free vertex and s l / 2 (13 doubles), so that
+// \int_T f . E dS = (s l / 2) sum_q w_q (r_q - v) . E(r_q) (rule weights sum to 1).
+__global__ void k_pw_surface(int m, const double* __restrict__ geo, V3 khat, V3 e0, double k0,
+                             double2 scale, double2* __restrict__ out) {
+    const DQuad& Q = c_rules[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int hf = 0; hf < 2; ++hf) {
+            const double* g = geo + (size_t)26 * i + 13 * hf;
+            const V3 a = v3(g), b = v3(g + 3), c = v3(g + 6), v = v3(g + 9);
+            const double sl2 = g[12];
+            for (int q = 0; q < Q.n; ++q) {
+                const V3 r = Q.b[q][0] * a + Q.b[q][1] * b + Q.b[q][2] * c;
+                double sn, cs;
+                sincos(k0 * dot(khat, r), &sn, &cs);
+                const double f = Q.w[q] * sl2 * dot(r - v, e0);
+                acc.x += f * cs;    // exp(-i phi) = cos phi - i sin phi
+                acc.y -= f * sn;
+            }
+        }
+        out[i] = cmul(scale, acc);
+    }
+}
+
+void planewave_surface(int m, const double* geo, const double khat[3], const double e0[3], double k0,
+                       double2 scale, double2* out, cudaStream_t st) {
+    upload_rules();
+    if (m <= 0) return;
+    const V3 kh = {khat[0], khat[1], khat[2]}, e = {e0[0], e0[1], e0[2]};
+    k_pw_surface<<<(m + 127) / 128, 128, 0, st>>>(m, geo, kh, e, k0, scale, out);
+    VSIE_CUDA(cudaGetLastError());
+}
+
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 127) / 128, 152 * 64); }
 
 void efie_block(const MeshDev& ma, const MeshDev& mb, bool same, int nr, const int* rows, int nc,

@@ -961,6 +961,30 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         }
         T.mark("block preconditioner");
     }
+    // RWG geometry for the plane-wave right-hand side (far first, then near)
+    {
+        std::vector<double> geo;
+        geo.reserve((size_t)26 * (m_f + m_n));
+        for (const MeshHost* mh : {&mh_s, &mh_c}) {
+            for (int i = 0; i < mh->m; ++i) {
+                const int tt[2] = {mh->tplus[i], mh->tminus[i]}, vv[2] = {mh->vplus[i], mh->vminus[i]};
+                for (int hf = 0; hf < 2; ++hf) {
+                    for (int k = 0; k < 3; ++k)
+                        for (int d = 0; d < 3; ++d) geo.push_back(mh->xyz[3 * (size_t)mh->tri[3 * tt[hf] + k] + d]);
+                    for (int d = 0; d < 3; ++d) geo.push_back(mh->xyz[3 * (size_t)vv[hf] + d]);
+                    geo.push_back((hf == 0 ? 0.5 : -0.5) * mh->len[i]);
+                }
+            }
+        }
+        if (!geo.empty()) {
+            try {
+                c->rwg_geo = up(*c, geo);
+            } catch (...) {
+                destroy_ctx(c);
+                throw;
+            }
+        }
+    }
     // ports: far ports first, then coil ports
     for (int e : mh_s.ports) {
         c->port_row.push_back(e);

@@ -49,5 +49,9 @@ void coupling_block(const MeshDev& m, const GridDev& g, int nvx, const int64_t* 
                     int64_t pstride, int only = -1);
 void field_points(const MeshDev& m, int np, const double* pts, int nc, const int* cols,
                   const double* ctr, double k0, double2* out);
+// out[m] = scale \int f_m . e0 exp(-i k0 khat . r) dS for m RWG functions
+// described by geo (26 doubles each: see k_pw_surface)
+void planewave_surface(int m, const double* geo, const double khat[3], const double e0[3], double k0,
+                       double2 scale, double2* out, cudaStream_t st);
 
 }  // namespace vsie

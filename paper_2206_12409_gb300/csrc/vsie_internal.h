@@ -207,6 +207,9 @@ struct Ctx {
     float* net_mat = nullptr;          // 2 x n_b: (eps_r - 1) / 50, sigma
     double* net_part = nullptr;        // reduction partials of the network's input scale
     float* net_scale = nullptr;        // per RHS: RMS of the Jacobi-scaled body residual
+    double* rwg_geo = nullptr;         // device, per RWG (far first, then near): per half
+                                       // T+, T- the 3 vertices, the free vertex, s l / 2
+                                       // (26 doubles); set by vsie_setup, else null
     vsie_parts parts_view{};           // filled by vsie_get_parts
     std::vector<std::complex<double>> hZff_copy;
 };

@@ -25,7 +25,7 @@ __all__ = [
     "sphere_phantom", "layered_head_phantom",
     "loop_strip", "closed_cylinder", "open_cylinder", "loop_array_on_cylinder",
     "merge_meshes", "random_vectors", "problem_sphere_loop_shield",
-    "problem_head", "problem_volume_only",
+    "problem_head", "problem_volume_only", "problem_coil_array_mid",
 ]
 
 
@@ -375,4 +375,23 @@ def problem_head(n_body=(96, 96, 112), h=2e-3, freq_hz=298e6, ext_n=(128, 128, 1
     shield = open_cylinder(0.33, 1.2, shield_theta, shield_z)
     off = tuple((e - b) // 2 for e, b in zip(ext_n, n_body))
     return Problem("head", g, er, sg, freq_hz, coil, shield, tuple(ext_n), off, 3,
+                   tt_tol, aca_tol, nrhs)
+
+
+def problem_coil_array_mid(n_body=(18, 18, 24), h=5e-3, freq_hz=298e6, ext_n=(26, 26, 24),
+                           n_loops=4, loop_seg=128, tt_tol=1e-6, aca_tol=1e-6, seed=3, nrhs=8):
+    """Mid-size workload with the structure of the head workload at a size the
+    oracle assembles in about a minute: a layered ellipsoid (semi-axes
+    40/40/52 mm, 5 mm and 10 mm shells, 2 mm RMS perturbation) on an 18 x 18 x 24
+    grid at 5 mm; a 4-loop strip array on a 55 mm cylinder (1024 triangles, 1024
+    RWG, 4 ports) close enough to the body for precorrection pairs; a closed
+    cylinder shield r = 0.1 m, L = 0.2 m of 1216 triangles (1824 RWG, not a
+    multiple of 256); extended grid 26 x 26 x 24 (FFT lengths 54, 54, 48)."""
+    g, er, sg = layered_head_phantom(n_body, h, (40e-3, 40e-3, 52e-3), (5e-3, 10e-3),
+                                     rms=2e-3, seed=seed)
+    coil = loop_array_on_cylinder(n_loops=n_loops, radius=0.055, height=0.08, width=3e-3,
+                                  gap=8e-3, corner=10e-3, n_seg=loop_seg)
+    shield = closed_cylinder(0.1, 0.2, n_theta=32, n_z=10, n_rings=5)
+    off = tuple((e - b) // 2 for e, b in zip(ext_n, n_body))
+    return Problem("coil_array_mid", g, er, sg, freq_hz, coil, shield, tuple(ext_n), off, 3,
                    tt_tol, aca_tol, nrhs)

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
                 7: "VSIE_EUNSUPPORTED"}
 
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
-           "vsie_matvec", "vsie_rhs_ports", "vsie_solve", "vsie_save", "vsie_load",
+           "vsie_matvec", "vsie_rhs_ports", "vsie_rhs_planewave", "vsie_solve", "vsie_save", "vsie_load",
            "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_volume_matvec_static",
            "vsie_net_create", "vsie_net_num_params", "vsie_net_set_params", "vsie_net_get_params",
            "vsie_net_forward", "vsie_net_backward", "vsie_net_step", "vsie_net_train",
@@ -106,6 +106,8 @@ def load_library(path: str | None = None):
     lib.vsie_matvec.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P]
     lib.vsie_rhs_ports.restype = C.c_int
     lib.vsie_rhs_ports.argtypes = [P, C.c_int32, C.POINTER(C.c_int32), C.c_double, P, C.c_int64, P]
+    lib.vsie_rhs_planewave.restype = C.c_int
+    lib.vsie_rhs_planewave.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), P, P]
     lib.vsie_solve.restype = C.c_int
     lib.vsie_solve.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_double,
                                C.POINTER(vsie_solve_opts), C.POINTER(vsie_solve_info), P]
@@ -296,6 +298,14 @@ def vsie_rhs_ports(ctx, ports, V, B, ldb, stream=0):
     pr = (C.c_int32 * len(ports))(*[int(x) for x in ports])
     _check(lib.vsie_rhs_ports(ctx, len(ports), pr, float(V), C.c_void_p(int(B)), int(ldb),
                               C.c_void_p(int(stream))), ctx)
+
+
+def vsie_rhs_planewave(ctx, k_hat, e0, B, stream=0):
+    """One plane-wave right-hand side column into device pointer B (N double2)."""
+    lib = load_library()
+    kh = (C.c_double * 3)(*[float(v) for v in k_hat])
+    ev = (C.c_double * 3)(*[float(v) for v in e0])
+    _check(lib.vsie_rhs_planewave(ctx, kh, ev, C.c_void_p(int(B)), C.c_void_p(int(stream))), ctx)
 
 
 def vsie_solve(ctx, p, B, ldb, X, ldx, tol, opts=None, stream=0, check=True):

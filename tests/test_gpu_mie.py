@@ -22,7 +22,7 @@ def test_sphere_plane_wave_vs_oracle_and_mie(N, eps, sig, mode):
     h = 2 * R / N
     g, er, sg = I.sphere_phantom(n=(N + 2,) * 3, h=h, radius=R, eps_r=eps, sigma=sig)
     prob = I.Problem("sphere", g, er, sg, F)
-    b = mie.body_rhs(g, er, sg, F)
+    b = mie.body_rhs(g, er, sg, F)     # the oracle's right-hand side for the oracle's solve
     # oracle solution of the same discrete system
     chi = physics.chi(er, sg, F)
     _, k0 = physics.omega_k0(F)
@@ -35,7 +35,11 @@ def test_sphere_plane_wave_vs_oracle_and_mie(N, eps, sig, mode):
     try:
         n_tot = V.vsie_sizes(ctx)[0]
         assert n_tot == 3 * g.nv
-        B = torch.from_numpy(b.copy()).cuda()[None, :]
+        # the library builds its own right-hand side for the incident plane wave
+        B = torch.full((1, n_tot), float("nan"), dtype=torch.complex128, device="cuda")
+        V.vsie_rhs_planewave(ctx, (0, 0, 1), (1, 0, 0), B.data_ptr())
+        torch.cuda.synchronize()
+        assert np.linalg.norm(B.cpu().numpy()[0] - b) <= 1e-12 * np.linalg.norm(b)
         X = torch.zeros_like(B)
         o = V.vsie_solve_opts()
         o.mode = mode

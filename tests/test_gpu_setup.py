@@ -7,7 +7,7 @@ import pytest
 
 from paper_2206_12409_gb300 import inputs as I
 from oracle import hybrid, coupling, rwg, tt as ott, physics
-from tests.conftest import gpu_matvec
+from tests.conftest import block_parity, gpu_matvec, output_blocks
 
 pytestmark = pytest.mark.gpu
 
@@ -84,6 +84,13 @@ def test_matvec_vs_oracle_hybrid_and_dense(setup_ctx, sphere_loop_shield, hybrid
     y = gpu_matvec(ctx, x, V.VSIE_C128)
     yh = hybrid.matvec(P, x)
     assert np.linalg.norm(y - yh) <= 2e-6 * np.linalg.norm(yh)
+    # per output block against the oracle's own parts: the set-up's parts are
+    # independent approximations (ACA, TT cross) at tolerance 1e-6 and a pFFT
+    # fit equal to the oracle's to ~1e-8, so every block agrees to ~1e-6
+    for name, rows in output_blocks(P).items():
+        e = np.linalg.norm((y - yh)[rows]) / np.linalg.norm(yh[rows])
+        print(f"[setup vs oracle parts] {name} rows: {e:.2e}")
+        assert e <= 1e-5, (name, e)
     Z, idx = dense_reference
     yd = hybrid.dense_matvec(sphere_loop_shield, Z, idx, x)
     assert np.linalg.norm(y - yd) <= 2e-3 * np.linalg.norm(yd)
@@ -111,3 +118,28 @@ def test_multi_rhs_matvec_equals_single_rhs(sphere_loop_shield, p):
             assert (torch.linalg.norm(Y - Y1) / torch.linalg.norm(Y1)).item() < tol
     finally:
         V.vsie_destroy(ctx)
+
+
+def _oracle_parts_with(P, g):
+    """The oracle's Parts with the operator parts the GPU set-up produced (its
+    projection, precorrection, near block, ACA factors, far block and TT cores);
+    spectra and materials stay the oracle's own."""
+    import dataclasses
+    import scipy.sparse as sp
+    nb = P.body.nv
+    if g.get("pre_nnz", 0):
+        pre = sp.csr_matrix((g["pre_val"], g["pre_col"], g["pre_rowptr"]), shape=(3 * nb, g["m_n"]))
+    else:
+        pre = sp.csr_matrix((3 * nb, g["m_n"]), dtype=np.complex128)
+    return dataclasses.replace(P, W=g["W"], base=g["base"], pre=pre, Znn=g["Znn"], U=g["U"],
+                               V=g["V"], Zff=g["Zff"], tt=g["tt"])
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 2e-5)])
+def test_matvec_blocks_with_setup_parts(setup_ctx, hybrid_parts, prec, tol):
+    """The matvec of a vsie_setup context, block by block, against the oracle's
+    matvec applied to the parts that set-up computed (the parts themselves are
+    checked against the oracle's in the tests above)."""
+    ctx, parts = setup_ctx
+    Pg = _oracle_parts_with(hybrid_parts, parts)
+    block_parity(ctx, Pg, prec, tol, p=2, seed=31, label="vsie_setup parts")
