@@ -9,7 +9,13 @@ and 6 surface points per triangle; "far" coupling (shield/bore <-> body, the
 entries that the TT approximates) with 1 volume point (voxel centre) and 1
 surface point (centroid).
 Pinned by: Gop f_n against a finite-difference curl-curl of the vector
-potential (tests/test_oracle_surface.py) and reciprocity with the EFIE block.
+potential (tests/test_oracle_surface.py); the near entries against a 10^3-point
+Gauss voxel rule on a refined triangle rule, whose difference falls like
+(h/d)^4 with distance, the order of a product rule exact for cubics; and
+reciprocity: the voxel-tested field of f_n equals the RWG-tested field of the
+voxel's uniform current computed from the dyadic Green's function
+(tests/test_oracle_coupling.py).  The far (1 x 1 point) entries are the
+definition of what the TT approximates and are pinned only through it.
 """
 from __future__ import annotations
 
