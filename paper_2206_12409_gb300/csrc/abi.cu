@@ -90,6 +90,29 @@ static cx<R>* up_c(Ctx& c, const std::vector<std::complex<double>>& h) {
     return upload(c, v.data(), v.size());
 }
 
+// Work buffers of the convolution: [chunk][3][n3][n2][L1] and
+// [chunk][3][n3][L2][L1] complex values.  The right-hand sides of one matvec are
+// processed in groups of `chunk` so that the buffers stay within kConvWorkBudget
+// bytes (a 1 mm head grid needs 2.1 GB per FP32 right-hand side).
+constexpr size_t kConvWorkBudget = 24ull << 30;
+
+static size_t conv_elems_A(const Ctx& c) { return 3 * (size_t)c.ne[2] * c.ne[1] * c.L[0]; }
+static size_t conv_elems_B(const Ctx& c) { return 3 * (size_t)c.ne[2] * c.L[1] * c.L[0]; }
+
+static int conv_chunk(const Ctx& c, size_t cs) {
+    const size_t per = (conv_elems_A(c) + conv_elems_B(c)) * cs;
+    const int most = (int)std::max<size_t>(1, std::min<size_t>((size_t)c.max_rhs, kConvWorkBudget / per));
+    const int groups = (c.max_rhs + most - 1) / most;
+    return (c.max_rhs + groups - 1) / groups;      // equal groups
+}
+static size_t conv_offB(const Ctx& c, size_t cs, int chunk) {
+    return ((size_t)chunk * conv_elems_A(c) * cs + 255) / 256 * 256;
+}
+static size_t conv_bytes(const Ctx& c, size_t cs) {
+    const int ch = conv_chunk(c, cs);
+    return conv_offB(c, cs, ch) + (size_t)ch * conv_elems_B(c) * cs;
+}
+
 template <typename R>
 static void prepare_precision(Ctx& c) {
     OpData<R>& d = data<R>(c);
@@ -154,12 +177,12 @@ static void prepare_precision(Ctx& c) {
             d.G[a][3] = up_c<R>(c, t);
         }
     }
-    // workspaces
+    // workspaces: the convolution's two work buffers for `chunk` right-hand sides
+    // inside the shared allocation (sized in init_ctx)
     const size_t p = c.max_rhs;
-    const size_t nA = p * 3 * (size_t)c.ne[2] * c.ne[1] * c.L[0];
-    const size_t nB = p * 3 * (size_t)c.ne[2] * c.L[1] * c.L[0];
-    d.bufA = (C*)dalloc(c, nA * sizeof(C));
-    d.bufB = (C*)dalloc(c, nB * sizeof(C));
+    d.chunk = conv_chunk(c, sizeof(C));
+    d.bufA = (C*)c.conv_work;
+    d.bufB = (C*)((char*)c.conv_work + conv_offB(c, sizeof(C), d.chunk));
     int r1 = 1, r2 = 1, r3 = 1;
     for (int a = 0; a < 3; ++a) {
         r1 = std::max(r1, c.tt_rank[a][0]);
@@ -398,6 +421,13 @@ static void init_ctx(Ctx& c, const vsie_grid* body, const double* eps_r, const d
                 c.hTT[a][q].assign(G, G + sz[q]);
             }
         }
+    }
+    {
+        size_t need = 0;
+        if (c.precisions & 2) need = std::max(need, conv_bytes(c, sizeof(float2)));
+        if (c.precisions & 1) need = std::max(need, conv_bytes(c, sizeof(double2)));
+        c.conv_work = dalloc(c, need);
+        c.conv_work_bytes = need;
     }
     if (c.precisions & 2) prepare_precision<float>(c);
     if (c.precisions & 1) prepare_precision<double>(c);

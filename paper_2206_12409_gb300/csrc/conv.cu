@@ -534,15 +534,26 @@ static void run_pass(const ConvArgs<R>& a, int p, int pass, int var, cudaStream_
 template <typename R>
 void conv_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
                 cudaStream_t st) {
-    const ConvArgs<R> a = make_args<R>(c, X, ldx, Y, ldy);
-    // algorithmic bytes of one launch group: the three-pass schedule moves
-    // 54 n_v complex values per RHS, plus the 6 spectrum octants once
+    ConvArgs<R> a = make_args<R>(c, X, ldx, Y, ldy);
+    OpData<R>& d = data<R>(c);
+    const int ch = d.chunk;
+    const int groups = (p + ch - 1) / ch;
+    // algorithmic bytes of the launch groups: the three-pass schedule moves
+    // 54 n_v complex values per RHS, plus the 6 spectrum octants once per group
     const double cs = sizeof(cx<R>);
-    const double alg = 54.0 * (double)c.n_e * cs * p + 6.0 * (double)c.Lh[0] * c.Lh[1] * c.Lh[2] * cs;
+    const double alg = 54.0 * (double)c.n_e * cs * p +
+                       6.0 * groups * (double)c.Lh[0] * c.Lh[1] * c.Lh[2] * cs;
     ProfScope ps(c, sizeof(R) == 4 ? PG_FFTCONV : PG_FFTCONV64, st, alg);
-    const int* tune = data<R>(c).tune;
-    for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, p, pass, tune[pass], st);
-    prof_count(c, 5);
+    const int* tune = d.tune;
+    for (int j0 = 0; j0 < p; j0 += ch) {
+        const int pj = std::min(ch, p - j0);
+        a.X = X + (size_t)j0 * ldx;
+        a.Y = Y + (size_t)j0 * ldy;
+        a.gc = d.gc + (size_t)j0 * 3 * c.nact;
+        a.cc = d.cc + (size_t)j0 * 3 * c.nact;
+        for (int pass = 0; pass < 5; ++pass) run_pass<R>(a, pj, pass, tune[pass], st);
+        prof_count(c, 5);
+    }
     VSIE_CUDA(cudaGetLastError());
 }
 
@@ -555,7 +566,7 @@ void conv_autotune(Ctx& c) {
     int dev = 0, smax = 0;
     VSIE_CUDA(cudaGetDevice(&dev));
     VSIE_CUDA(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int p = std::min(c.max_rhs, 4);
+    const int p = std::min(d.chunk, 4);
     cx<R>* xy = (cx<R>*)dalloc(c, (size_t)2 * c.N * p * sizeof(cx<R>));
     VSIE_CUDA(cudaMemset(xy, 0, (size_t)2 * c.N * p * sizeof(cx<R>)));
     const ConvArgs<R> a = make_args<R>(c, xy, c.N, xy + (size_t)c.N * p, c.N);

@@ -111,8 +111,9 @@ struct OpData {
     cx<R>* Zff = nullptr;
     cx<R>* G[3][4] = {{nullptr}};   // TT cores; G[c][3] stored transposed (m_f x r3)
     // workspaces
-    cx<R>* bufA = nullptr;      // [p][3][n3][n2][L1]
-    cx<R>* bufB = nullptr;      // [p][3][n3][L2][L1]
+    cx<R>* bufA = nullptr;      // [chunk][3][n3][n2][L1]  (in Ctx::conv_work, shared
+    cx<R>* bufB = nullptr;      // [chunk][3][n3][L2][L1]   by both precisions)
+    int chunk = 1;              // right-hand sides per launch group of the convolution
     cx<R>* gc = nullptr;        // [p][3][nact] coil contributions on active voxels
     cx<R>* cc = nullptr;        // [p][3][nact] convolution on active voxels
     cx<R>* t1 = nullptr;        // small GEMM intermediates
@@ -196,6 +197,8 @@ struct Ctx {
     OpData<float> f32;
     OpData<double> f64;
     std::vector<void*> allocs;         // every device allocation (freed at destroy)
+    void* conv_work = nullptr;         // FFT work buffers of the convolution (both precisions:
+    size_t conv_work_bytes = 0;        // FP32 and FP64 matvecs never run at the same time)
     // solver scratch (FP64)
     double2* kr_V = nullptr;           // Krylov basis
     double2* kr_Z = nullptr;           // flexible directions (FP32 stored as float2)
