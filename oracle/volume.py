@@ -143,3 +143,37 @@ def fft_matvec(grid, chi, k0, x, spec=None):
     d = np.tile(invchi, 3)[:, None]
     y = np.where(M3[:, None], h3 * (d * x - c), x)
     return y
+
+
+def rows_matvec(grid, chi, k0, x, rows, chunk=1 << 20):
+    """Selected rows of y = Z_bb x by direct summation over every material
+    voxel (the definition, no FFT): for row r = a * nv + p,
+        y_r = h^3 x_r / chi_p - h^3 sum_{q, b} T_ab(p - q) x_{b, q}   (p material),
+        y_r = x_r                                                    (p vacuum).
+    Used where the FFT oracle does not fit the host (grids of ~10^7 voxels).
+    x: (3 nv, k); returns (len(rows), k).  Pinned by dense_matvec
+    (tests/test_oracle_volume.py)."""
+    chi = np.asarray(chi)
+    nv = grid.nv
+    n1, n2, _ = grid.n
+    x = np.asarray(x, np.complex128).reshape(3 * nv, -1)
+    M = material_mask(chi)
+    idx = np.nonzero(M)[0]
+    qi = np.stack([idx % n1, (idx // n1) % n2, idx // (n1 * n2)], -1)
+    xs = [x[b * nv + idx] for b in range(3)]          # (m, k) per component
+    h3 = grid.h ** 3
+    out = np.zeros((len(rows), x.shape[1]), np.complex128)
+    for i, r in enumerate(rows):
+        a, p = divmod(int(r), nv)
+        if not M[p]:
+            out[i] = x[r]
+            continue
+        pi = np.array([p % n1, (p // n1) % n2, p // (n1 * n2)])
+        acc = np.zeros(x.shape[1], np.complex128)
+        for c0 in range(0, idx.size, chunk):
+            sl = slice(c0, c0 + chunk)
+            T = physics.voxel_kernel(pi[None, :] - qi[sl], grid.h, k0)     # (c, 3, 3)
+            for b in range(3):
+                acc += T[:, a, b] @ xs[b][sl]
+        out[i] = h3 * (x[r] / chi[p] - acc)
+    return out

@@ -16,6 +16,9 @@
 // input once and its output once.  Shared memory holds [k][line] tiles.
 #include "fft.cuh"
 
+#include <cstdio>
+#include <cstdlib>
+
 namespace vsie {
 
 template <typename R>
@@ -56,6 +59,10 @@ template <typename C>
 __device__ __forceinline__ void load_tw(C* s, const C* g, int L) {
     for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = g[i];
 }
+
+}  // namespace vsie
+#include "conv_reg.cuh"
+namespace vsie {
 
 // --------------------------------------------------------------- X forward
 template <typename R, int NL>
@@ -440,6 +447,13 @@ static const Variant kXV[] = {{8, 128}, {8, 256}, {16, 256}, {16, 512}, {32, 512
 static const Variant kZV[] = {{4, 256}, {4, 384}, {4, 512}, {8, 512}, {8, 768}, {8, 1024}, {16, 1024}};
 constexpr int kNX = sizeof(kXV) / sizeof(kXV[0]);
 constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
+// Register-resident FP32 kernels (conv_reg.cuh) for the lengths they are built
+// for, appended after the generic variants of each pass: x and y passes take NL
+// lines per CTA (16 NL threads), the z pass NT threads per CTA (16 lines for
+// M = 112, 8 for M = 224).
+static const int kXR[] = {8, 16, 32};
+static const int kZR[] = {256, 384, 512};
+constexpr int kNR = 3;
 
 template <typename R>
 static ConvArgs<R> make_args(Ctx& c, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy) {
@@ -494,6 +508,81 @@ static void launch_z(const ConvArgs<R>& a, int p, int t, cudaStream_t st) {
     k_zmul<R, NL><<<g, t, sm, st>>>(a);
 }
 
+// ---- register variants (FP32): applicability, shared memory, launch
+static bool reg_len_ok(int L) { return L == 256 || L == 512; }
+static int reg_zR2(const ConvArgs<float>& a) {
+    if (!a.zhalf) return 0;
+    return a.L3 == 224 ? 7 : a.L3 == 448 ? 14 : 0;
+}
+static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
+    const size_t cs = sizeof(float2);
+    if (pass == 0 || pass == 4) {
+        if (!reg_len_ok(a.L1)) return 0;
+        const size_t L = a.L1, NL = kXR[rv], R1 = L / 16;
+        return (L + NL * (L / 2 + 1) + NL * 16 * (R1 + 1)) * cs;
+    }
+    if (pass == 1 || pass == 3) {
+        if (!reg_len_ok(a.L2)) return 0;
+        return ((size_t)a.L2 + (size_t)kXR[rv] * a.L2) * cs;
+    }
+    const int R2 = reg_zR2(a);
+    if (!R2) return 0;
+    const size_t M = 16 * R2, NL = R2 == 7 ? 16 : 8;
+    return (2 * M + 2 * 6 * M * NL) * cs;
+}
+
+template <int R1, int NL>
+static void launch_xreg(const ConvArgs<float>& a, int p, bool inv, cudaStream_t st) {
+    const size_t sm = reg_smem(a, inv ? 4 : 0, NL == 8 ? 0 : NL == 16 ? 1 : 2);
+    dim3 g((a.n2 * a.n3 + NL - 1) / NL, 3, p);
+    if (inv) k_xinv_reg<R1, 16, NL><<<g, 16 * NL, sm, st>>>(a);
+    else k_xfwd_reg<R1, 16, NL><<<g, 16 * NL, sm, st>>>(a);
+}
+template <int R1, int NL>
+static void launch_yreg(const ConvArgs<float>& a, int p, bool inv, cudaStream_t st) {
+    const size_t sm = ((size_t)a.L2 + (size_t)NL * a.L2) * sizeof(float2);
+    dim3 g((a.L1 + NL - 1) / NL, a.n3, 3 * p);
+    if (inv) k_yreg<R1, 16, NL, true, false><<<g, 16 * NL, sm, st>>>(a);
+    else k_yreg<R1, 16, NL, false, true><<<g, 16 * NL, sm, st>>>(a);
+}
+template <int R2, int NT>
+static void launch_zreg(const ConvArgs<float>& a, int p, cudaStream_t st) {
+    constexpr int NL = R2 == 7 ? 16 : 8;
+    const size_t sm = reg_smem(a, 2, 0);
+    dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
+    k_zreg<R2, NL, NT><<<g, NT, sm, st>>>(a);
+}
+template <int NL>
+static void launch_xyreg(const ConvArgs<float>& a, int p, int pass, cudaStream_t st) {
+    if (pass == 0 || pass == 4) {
+        if (a.L1 == 256) launch_xreg<16, NL>(a, p, pass == 4, st);
+        else launch_xreg<32, NL>(a, p, pass == 4, st);
+    } else {
+        if (a.L2 == 256) launch_yreg<16, NL>(a, p, pass == 3, st);
+        else launch_yreg<32, NL>(a, p, pass == 3, st);
+    }
+}
+static void run_reg_pass(const ConvArgs<float>& a, int p, int pass, int rv, cudaStream_t st) {
+    if (pass == 2) {
+        const int R2 = reg_zR2(a);
+        if (R2 == 7) {
+            if (rv == 0) launch_zreg<7, 256>(a, p, st);
+            else if (rv == 1) launch_zreg<7, 384>(a, p, st);
+            else launch_zreg<7, 512>(a, p, st);
+        } else {
+            if (rv == 0) launch_zreg<14, 256>(a, p, st);
+            else if (rv == 1) launch_zreg<14, 384>(a, p, st);
+            else launch_zreg<14, 512>(a, p, st);
+        }
+        return;
+    }
+    switch (kXR[rv]) {
+        case 8: launch_xyreg<8>(a, p, pass, st); break;
+        case 16: launch_xyreg<16>(a, p, pass, st); break;
+        default: launch_xyreg<32>(a, p, pass, st); break;
+    }
+}
+
 template <typename R>
 static size_t smem_of(const ConvArgs<R>& a, int pass, int nl) {
     const size_t cs = sizeof(cx<R>);
@@ -505,6 +594,11 @@ static size_t smem_of(const ConvArgs<R>& a, int pass, int nl) {
 // pass: 0 X-fwd, 1 Y-fwd, 2 Z, 3 Y-inv, 4 X-inv
 template <typename R>
 static void run_pass(const ConvArgs<R>& a, int p, int pass, int var, cudaStream_t st) {
+    const int ng = pass == 2 ? kNZ : kNX;
+    if (var >= ng) {
+        if constexpr (sizeof(R) == 4) run_reg_pass(a, p, pass, var - ng, st);
+        return;
+    }
     if (pass == 2) {
         const Variant v = kZV[var];
         switch (v.nl) {
@@ -573,15 +667,28 @@ void conv_autotune(Ctx& c) {
     cudaEvent_t e0, e1;
     VSIE_CUDA(cudaEventCreate(&e0));
     VSIE_CUDA(cudaEventCreate(&e1));
+    std::string why = "no variant's shared memory fits";
     for (int pass = 0; pass < 5; ++pass) {
-        const int nv = pass == 2 ? kNZ : kNX;
+        const int ng = pass == 2 ? kNZ : kNX;
+        const int nv = ng + (sizeof(R) == 4 ? kNR : 0);
         float best = 1e30f;
         int bi = -1;
         for (int v = 0; v < nv; ++v) {
-            const int nl = pass == 2 ? kZV[v].nl : kXV[v].nl;
-            if (smem_of(a, pass, nl) > (size_t)smax) continue;
+            if (v < ng) {
+                const int nl = pass == 2 ? kZV[v].nl : kXV[v].nl;
+                if (smem_of(a, pass, nl) > (size_t)smax) continue;
+            } else {
+                if constexpr (sizeof(R) == 4) {
+                    const size_t sm = reg_smem(a, pass, v - ng);
+                    if (sm == 0 || sm > (size_t)smax) continue;
+                }
+            }
             run_pass<R>(a, p, pass, v, 0);   // warm-up
-            if (cudaGetLastError() != cudaSuccess) continue;
+            const cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) {
+                why = std::string(cudaGetErrorString(le)) + " (variant " + std::to_string(v) + ")";
+                continue;
+            }
             VSIE_CUDA(cudaEventRecord(e0, 0));
             for (int it = 0; it < 3; ++it) run_pass<R>(a, p, pass, v, 0);
             VSIE_CUDA(cudaEventRecord(e1, 0));
@@ -595,9 +702,17 @@ void conv_autotune(Ctx& c) {
         if (bi < 0) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            throw Error(VSIE_EUNSUPPORTED, "no FFT pass configuration fits this grid");
+            throw Error(VSIE_EUNSUPPORTED, "no FFT pass configuration fits this grid (pass " +
+                                               std::to_string(pass) + ", precision " +
+                                               std::to_string(sizeof(R) * 16) + " bits: " + why + ")");
         }
         d.tune[pass] = bi;
+        if (std::getenv("VSIE_TRACE_TUNE")) {
+            fprintf(stderr, "[vsie tune] FP%d pass %d L=(%d,%d,%d) p=%d chosen %d:", (int)sizeof(R) * 8, pass,
+                    c.L[0], c.L[1], c.L[2], p, bi);
+            for (int v = 0; v < nv; ++v) fprintf(stderr, " %.3f", d.tune_ms[pass][v]);
+            fprintf(stderr, "\n");
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -612,6 +727,20 @@ void conv_set_attrs() {
     VSIE_ATTR((k_ypass<R, 8, false>)); VSIE_ATTR((k_ypass<R, 16, false>)); VSIE_ATTR((k_ypass<R, 32, false>));
     VSIE_ATTR((k_ypass<R, 8, true>)); VSIE_ATTR((k_ypass<R, 16, true>)); VSIE_ATTR((k_ypass<R, 32, true>));
     VSIE_ATTR((k_zmul<R, 4>)); VSIE_ATTR((k_zmul<R, 8>)); VSIE_ATTR((k_zmul<R, 16>));
+    if constexpr (sizeof(R) == 4) {
+        VSIE_ATTR((k_xfwd_reg<16, 16, 8>)); VSIE_ATTR((k_xfwd_reg<16, 16, 16>)); VSIE_ATTR((k_xfwd_reg<16, 16, 32>));
+        VSIE_ATTR((k_xfwd_reg<32, 16, 8>)); VSIE_ATTR((k_xfwd_reg<32, 16, 16>)); VSIE_ATTR((k_xfwd_reg<32, 16, 32>));
+        VSIE_ATTR((k_xinv_reg<16, 16, 8>)); VSIE_ATTR((k_xinv_reg<16, 16, 16>)); VSIE_ATTR((k_xinv_reg<16, 16, 32>));
+        VSIE_ATTR((k_xinv_reg<32, 16, 8>)); VSIE_ATTR((k_xinv_reg<32, 16, 16>)); VSIE_ATTR((k_xinv_reg<32, 16, 32>));
+        VSIE_ATTR((k_yreg<16, 16, 8, false, true>)); VSIE_ATTR((k_yreg<16, 16, 16, false, true>));
+        VSIE_ATTR((k_yreg<16, 16, 32, false, true>)); VSIE_ATTR((k_yreg<32, 16, 8, false, true>));
+        VSIE_ATTR((k_yreg<32, 16, 16, false, true>)); VSIE_ATTR((k_yreg<32, 16, 32, false, true>));
+        VSIE_ATTR((k_yreg<16, 16, 8, true, false>)); VSIE_ATTR((k_yreg<16, 16, 16, true, false>));
+        VSIE_ATTR((k_yreg<16, 16, 32, true, false>)); VSIE_ATTR((k_yreg<32, 16, 8, true, false>));
+        VSIE_ATTR((k_yreg<32, 16, 16, true, false>)); VSIE_ATTR((k_yreg<32, 16, 32, true, false>));
+        VSIE_ATTR((k_zreg<7, 16, 256>)); VSIE_ATTR((k_zreg<7, 16, 384>)); VSIE_ATTR((k_zreg<7, 16, 512>));
+        VSIE_ATTR((k_zreg<14, 8, 256>)); VSIE_ATTR((k_zreg<14, 8, 384>)); VSIE_ATTR((k_zreg<14, 8, 512>));
+    }
 #undef VSIE_ATTR
 }
 

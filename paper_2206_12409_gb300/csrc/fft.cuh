@@ -177,6 +177,53 @@ template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<5>) { dft_odd<INV, 5>(v); }
 template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<7>) { dft_odd<INV, 7>(v); }
 
+// radix 2R from two radix-R transforms of the even and odd samples:
+// X[k] = E[k] + w^k O[k], X[k + R] = E[k] - w^k O[k],  w = exp(-+ 2 pi i / (2R)),
+// with c[k] = cos(pi k / R), s[k] = sin(pi k / R)
+template <bool INV, int RH, typename C, typename R>
+__device__ __forceinline__ void dft_even_odd(C* v, const R* c, const R* s) {
+    C e[RH], o[RH];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) {
+        e[r] = v[2 * r];
+        o[r] = v[2 * r + 1];
+    }
+    dftR<INV>(e, int_<RH>());
+    dftR<INV>(o, int_<RH>());
+#pragma unroll
+    for (int k = 0; k < RH; ++k) {
+        const C t = k == 0 ? o[0] : twc<INV>(o[k], c[k], s[k]);
+        v[k] = cadd(e[k], t);
+        v[k + RH] = csub(e[k], t);
+    }
+}
+
+// radix 14 = 2 x 7
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<14>) {
+    using R = decltype(v[0].x);
+    const R c[7] = {(R)1.0, (R)0.90096886790241912624, (R)0.62348980185873353053, (R)0.22252093395631440429,
+                    (R)-0.22252093395631440429, (R)-0.62348980185873353053, (R)-0.90096886790241912624};
+    const R s[7] = {(R)0.0, (R)0.43388373911755812048, (R)0.78183148246802980871, (R)0.97492791218182360702,
+                    (R)0.97492791218182360702, (R)0.78183148246802980871, (R)0.43388373911755812048};
+    dft_even_odd<INV, 7>(v, c, s);
+}
+
+// radix 32 = 2 x 16
+template <bool INV, typename C> __device__ __forceinline__ void dftR(C* v, int_<32>) {
+    using R = decltype(v[0].x);
+    const R c[16] = {(R)1.0, (R)0.98078528040323044913, (R)0.92387953251128675613, (R)0.83146961230254523708,
+                     (R)0.70710678118654752440, (R)0.55557023301960222474, (R)0.38268343236508977173,
+                     (R)0.19509032201612826785, (R)0.0, (R)-0.19509032201612826785, (R)-0.38268343236508977173,
+                     (R)-0.55557023301960222474, (R)-0.70710678118654752440, (R)-0.83146961230254523708,
+                     (R)-0.92387953251128675613, (R)-0.98078528040323044913};
+    const R s[16] = {(R)0.0, (R)0.19509032201612826785, (R)0.38268343236508977173, (R)0.55557023301960222474,
+                     (R)0.70710678118654752440, (R)0.83146961230254523708, (R)0.92387953251128675613,
+                     (R)0.98078528040323044913, (R)1.0, (R)0.98078528040323044913, (R)0.92387953251128675613,
+                     (R)0.83146961230254523708, (R)0.70710678118654752440, (R)0.55557023301960222474,
+                     (R)0.38268343236508977173, (R)0.19509032201612826785};
+    dft_even_odd<INV, 16>(v, c, s);
+}
+
 template <int RR, bool INV, int NLT, int KS, typename C>
 __device__ __forceinline__ void stage_pp(const C* __restrict__ src, C* __restrict__ dst, int L,
                                          int Ns, uint32_t nsmagic, int twstep,

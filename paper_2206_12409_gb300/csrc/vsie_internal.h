@@ -126,7 +126,7 @@ struct OpData {
     cx<R>* pc_Znni = nullptr;   // Z_nn^-1 (m_n x m_n)
     cx<R>* pc_bdiag = nullptr;  // inverse body diagonal (n_b)
     int tune[5] = {0, 0, 0, 0, 0};     // chosen FFT pass variants (autotuned)
-    float tune_ms[5][8] = {{0}};       // measured time per variant (ms, p = min(max_rhs, 4))
+    float tune_ms[5][16] = {{0}};      // measured time per variant (ms, p = min(chunk, 4))
     bool ready = false;
 };
 

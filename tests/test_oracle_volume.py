@@ -97,3 +97,18 @@ def test_clausius_mossotti_limit_converges():
         E = j[:m] / (1j * w * physics.EPS0 * chi[idx])
         errs.append(abs(E.mean() - 3 / 52) / (3 / 52))
     assert errs[0] < 0.10 and errs[1] < errs[0]
+
+
+def test_rows_matvec_equals_dense():
+    """The direct-sum rows (used for sampled checks on grids the FFT oracle does
+    not fit) equal the brute-force dense matvec, vacuum rows included."""
+    from oracle import volume, physics
+    from paper_2206_12409_gb300 import inputs as I
+    g, er, sg = I.sphere_phantom((7, 6, 5), 5e-3, 14e-3, 50.0, 0.6)
+    chi = physics.chi(er, sg, 298e6)
+    _, k0 = physics.omega_k0(298e6)
+    x = I.random_vectors(3 * g.nv, 2, seed=5)
+    yd = volume.dense_matvec(g, chi, k0, x)
+    rows = np.array([0, 17, g.nv + 44, 2 * g.nv + 101, 3 * g.nv - 1, int(np.argmax(chi != 0))])
+    yr = volume.rows_matvec(g, chi, k0, x, rows, chunk=37)
+    assert np.max(np.abs(yr - yd[rows])) <= 1e-13 * np.max(np.abs(yd))
