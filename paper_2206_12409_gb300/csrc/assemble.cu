@@ -410,6 +410,95 @@ void planewave_surface(int m, const double* geo, const double khat[3], const dou
     VSIE_CUDA(cudaGetLastError());
 }
 
+// Grid part of the near block, summed directly over stencil pairs (the pFFT
+// reading of Sec. III with Z_nn dense): for near RWG m, n with stencils S_m, S_n
+// (voxel s^3 blocks at base_m, base_n of the extended grid) and weights W,
+//   Z[m + ld n] += h^3 sum_{a, q in S_m} sum_{b, q' in S_n}
+//                  W[m][a s^3 + q] T_ab(q - q') W[n][b s^3 + q'],
+// with T the voxel kernel of the body operator (T(d) = h^3 (k0^2 + grad grad) g
+// at d h, the equal-volume-sphere self term at d = 0).  This equals h^3 P^T K P
+// through the aperiodic grid convolution exactly (the embedding adds no
+// periodic images), at a cost of m_n^2 (2 s - 1)^3 kernel values.  One CTA per
+// row m (its weights in shared memory), threads over n.
+__device__ void voxel_kernel6(int dx, int dy, int dz, double h, double k0, double2 selfv, double2 T[6]) {
+    if (dx == 0 && dy == 0 && dz == 0) {
+        T[0] = T[1] = T[2] = selfv;
+        T[3] = T[4] = T[5] = make_double2(0.0, 0.0);
+        return;
+    }
+    const double rx = h * dx, ry = h * dy, rz = h * dz;
+    const double R2 = rx * rx + ry * ry + rz * rz;
+    const double R = sqrt(R2);
+    double sn, cs;
+    sincos(k0 * R, &sn, &cs);
+    const double pre = h * h * h / (4.0 * M_PI * R * R2);
+    const double2 g = make_double2(pre * cs, -pre * sn);
+    const double kR = k0 * R;
+    const double2 A = cmul(g, make_double2(kR * kR - 1.0, -kR));
+    const double2 B = cmul(g, make_double2(3.0 - kR * kR, 3.0 * kR));
+    const double ux = rx / R, uy = ry / R, uz = rz / R;
+    T[0] = cadd(A, cscale(B, ux * ux));
+    T[1] = cadd(A, cscale(B, uy * uy));
+    T[2] = cadd(A, cscale(B, uz * uz));
+    T[3] = cscale(B, ux * uy);
+    T[4] = cscale(B, ux * uz);
+    T[5] = cscale(B, uy * uz);
+}
+
+__global__ void k_ptkp(int mn, int s, const double2* __restrict__ W, const int* __restrict__ base, double h,
+                       double k0, double2 selfv, double2* __restrict__ Z, int64_t ldz) {
+    extern __shared__ __align__(16) unsigned char ptkp_smem[];
+    double2* wm = reinterpret_cast<double2*>(ptkp_smem);
+    const int s3 = s * s * s, m = blockIdx.x;
+    for (int i = threadIdx.x; i < 3 * s3; i += blockDim.x) wm[i] = W[(size_t)m * 3 * s3 + i];
+    const int bm0 = base[3 * m], bm1 = base[3 * m + 1], bm2 = base[3 * m + 2];
+    __syncthreads();
+    const double h3 = h * h * h;
+    for (int n = threadIdx.x; n < mn; n += blockDim.x) {
+        const double2* wn = W + (size_t)n * 3 * s3;
+        const int d0 = bm0 - base[3 * n], d1 = bm1 - base[3 * n + 1], d2 = bm2 - base[3 * n + 2];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int ez = 1 - s; ez < s; ++ez)
+            for (int ey = 1 - s; ey < s; ++ey)
+                for (int ex = 1 - s; ex < s; ++ex) {
+                    // q - q' = (ex, ey, ez) within the stencils
+                    double2 T[6];
+                    voxel_kernel6(d0 + ex, d1 + ey, d2 + ez, h, k0, selfv, T);
+                    double2 C[3][3];
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) C[a][b] = make_double2(0.0, 0.0);
+                    for (int qz = max(0, ez); qz < min(s, s + ez); ++qz)
+                        for (int qy = max(0, ey); qy < min(s, s + ey); ++qy)
+                            for (int qx = max(0, ex); qx < min(s, s + ex); ++qx) {
+                                const int q = qx + s * (qy + s * qz);
+                                const int qq = (qx - ex) + s * ((qy - ey) + s * (qz - ez));
+                                for (int a = 0; a < 3; ++a) {
+                                    const double2 wa = wm[a * s3 + q];
+                                    for (int b = 0; b < 3; ++b) cfma(C[a][b], wa, wn[b * s3 + qq]);
+                                }
+                            }
+                    // sum_ab T_ab C_ab with T symmetric: xx yy zz xy xz yz
+                    cfma(acc, T[0], C[0][0]);
+                    cfma(acc, T[1], C[1][1]);
+                    cfma(acc, T[2], C[2][2]);
+                    cfma(acc, T[3], cadd(C[0][1], C[1][0]));
+                    cfma(acc, T[4], cadd(C[0][2], C[2][0]));
+                    cfma(acc, T[5], cadd(C[1][2], C[2][1]));
+                }
+        double2* z = Z + (size_t)m + (size_t)n * ldz;
+        *z = cadd(*z, cscale(acc, h3));
+    }
+}
+
+void ptkp_add(int mn, int s, const double2* W, const int* base, double h, double k0, double2 selfv, double2* Z,
+              int64_t ldz) {
+    if (mn <= 0) return;
+    const size_t sm = (size_t)3 * s * s * s * sizeof(double2);
+    if (sm > 48 * 1024) VSIE_CUDA(cudaFuncSetAttribute(k_ptkp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_ptkp<<<mn, 128, sm>>>(mn, s, W, base, h, k0, selfv, Z, ldz);
+    VSIE_CUDA(cudaGetLastError());
+}
+
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 127) / 128, 152 * 64); }
 
 void efie_block(const MeshDev& ma, const MeshDev& mb, bool same, int nr, const int* rows, int nc,

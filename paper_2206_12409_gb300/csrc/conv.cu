@@ -449,10 +449,9 @@ constexpr int kNX = sizeof(kXV) / sizeof(kXV[0]);
 constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
 // Register-resident FP32 kernels (conv_reg.cuh) for the lengths they are built
 // for, appended after the generic variants of each pass: x and y passes take NL
-// lines per CTA (16 NL threads), the z pass NT threads per CTA (16 lines for
-// M = 112, 8 for M = 224).
+// lines per CTA (16 NL threads), the z pass NL = 4, 8, 16 lines (M = 112) or
+// NL = 2, 4, 8 (M = 224) per CTA with 32 NL threads.
 static const int kXR[] = {8, 16, 32};
-static const int kZR[] = {256, 384, 512};
 constexpr int kNR = 3;
 
 template <typename R>
@@ -514,6 +513,7 @@ static int reg_zR2(const ConvArgs<float>& a) {
     if (!a.zhalf) return 0;
     return a.L3 == 224 ? 7 : a.L3 == 448 ? 14 : 0;
 }
+static int reg_zNL(int R2, int rv) { return (R2 == 7 ? 4 : 2) << rv; }
 static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
     const size_t cs = sizeof(float2);
     if (pass == 0 || pass == 4) {
@@ -527,8 +527,8 @@ static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
     }
     const int R2 = reg_zR2(a);
     if (!R2) return 0;
-    const size_t M = 16 * R2, NL = R2 == 7 ? 16 : 8;
-    return (2 * M + 2 * 6 * M * NL) * cs;
+    const size_t M = 16 * R2, NL = reg_zNL(R2, rv);
+    return (2 * M + 6 * M * NL) * cs;
 }
 
 template <int R1, int NL>
@@ -545,12 +545,11 @@ static void launch_yreg(const ConvArgs<float>& a, int p, bool inv, cudaStream_t 
     if (inv) k_yreg<R1, 16, NL, true, false><<<g, 16 * NL, sm, st>>>(a);
     else k_yreg<R1, 16, NL, false, true><<<g, 16 * NL, sm, st>>>(a);
 }
-template <int R2, int NT>
+template <int R2, int NL>
 static void launch_zreg(const ConvArgs<float>& a, int p, cudaStream_t st) {
-    constexpr int NL = R2 == 7 ? 16 : 8;
-    const size_t sm = reg_smem(a, 2, 0);
+    const size_t sm = (size_t)(2 * 16 * R2 + 6 * 16 * R2 * NL) * sizeof(float2);
     dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
-    k_zreg<R2, NL, NT><<<g, NT, sm, st>>>(a);
+    k_zreg<R2, NL><<<g, 32 * NL, sm, st>>>(a);
 }
 template <int NL>
 static void launch_xyreg(const ConvArgs<float>& a, int p, int pass, cudaStream_t st) {
@@ -566,13 +565,13 @@ static void run_reg_pass(const ConvArgs<float>& a, int p, int pass, int rv, cuda
     if (pass == 2) {
         const int R2 = reg_zR2(a);
         if (R2 == 7) {
-            if (rv == 0) launch_zreg<7, 256>(a, p, st);
-            else if (rv == 1) launch_zreg<7, 384>(a, p, st);
-            else launch_zreg<7, 512>(a, p, st);
+            if (rv == 0) launch_zreg<7, 4>(a, p, st);
+            else if (rv == 1) launch_zreg<7, 8>(a, p, st);
+            else launch_zreg<7, 16>(a, p, st);
         } else {
-            if (rv == 0) launch_zreg<14, 256>(a, p, st);
-            else if (rv == 1) launch_zreg<14, 384>(a, p, st);
-            else launch_zreg<14, 512>(a, p, st);
+            if (rv == 0) launch_zreg<14, 2>(a, p, st);
+            else if (rv == 1) launch_zreg<14, 4>(a, p, st);
+            else launch_zreg<14, 8>(a, p, st);
         }
         return;
     }
@@ -727,6 +726,7 @@ void conv_set_attrs() {
     VSIE_ATTR((k_ypass<R, 8, false>)); VSIE_ATTR((k_ypass<R, 16, false>)); VSIE_ATTR((k_ypass<R, 32, false>));
     VSIE_ATTR((k_ypass<R, 8, true>)); VSIE_ATTR((k_ypass<R, 16, true>)); VSIE_ATTR((k_ypass<R, 32, true>));
     VSIE_ATTR((k_zmul<R, 4>)); VSIE_ATTR((k_zmul<R, 8>)); VSIE_ATTR((k_zmul<R, 16>));
+    VSIE_ATTR((k_zmul_h<R, 4>)); VSIE_ATTR((k_zmul_h<R, 8>)); VSIE_ATTR((k_zmul_h<R, 16>));
     if constexpr (sizeof(R) == 4) {
         VSIE_ATTR((k_xfwd_reg<16, 16, 8>)); VSIE_ATTR((k_xfwd_reg<16, 16, 16>)); VSIE_ATTR((k_xfwd_reg<16, 16, 32>));
         VSIE_ATTR((k_xfwd_reg<32, 16, 8>)); VSIE_ATTR((k_xfwd_reg<32, 16, 16>)); VSIE_ATTR((k_xfwd_reg<32, 16, 32>));
@@ -738,8 +738,8 @@ void conv_set_attrs() {
         VSIE_ATTR((k_yreg<16, 16, 8, true, false>)); VSIE_ATTR((k_yreg<16, 16, 16, true, false>));
         VSIE_ATTR((k_yreg<16, 16, 32, true, false>)); VSIE_ATTR((k_yreg<32, 16, 8, true, false>));
         VSIE_ATTR((k_yreg<32, 16, 16, true, false>)); VSIE_ATTR((k_yreg<32, 16, 32, true, false>));
-        VSIE_ATTR((k_zreg<7, 16, 256>)); VSIE_ATTR((k_zreg<7, 16, 384>)); VSIE_ATTR((k_zreg<7, 16, 512>));
-        VSIE_ATTR((k_zreg<14, 8, 256>)); VSIE_ATTR((k_zreg<14, 8, 384>)); VSIE_ATTR((k_zreg<14, 8, 512>));
+        VSIE_ATTR((k_zreg<7, 4>)); VSIE_ATTR((k_zreg<7, 8>)); VSIE_ATTR((k_zreg<7, 16>));
+        VSIE_ATTR((k_zreg<14, 2>)); VSIE_ATTR((k_zreg<14, 4>)); VSIE_ATTR((k_zreg<14, 8>));
     }
 #undef VSIE_ATTR
 }

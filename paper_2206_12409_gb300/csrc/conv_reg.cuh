@@ -242,18 +242,18 @@ __global__ void __launch_bounds__(R2 * NL) k_xinv_reg(ConvArgs<float> a) {
 }
 
 // --------------------------------------------------------------- z pass
-// CTA: NL consecutive k1 columns at one k2, all three components, one RHS; NT
-// threads.  Shared memory: twiddles (L3), forward exchange and inverse exchange,
-// each [component][even/odd][m][line] with m in [0, M).
-template <int R2, int NL, int NT>
-__global__ void __launch_bounds__(NT) k_zreg(ConvArgs<float> a) {
+// CTA: NL consecutive k1 columns at one k2, all three components, one RHS;
+// 32 NL threads, one (even/odd half, k1, line) item each in the middle phase.
+// Shared memory: twiddles (L3) and one exchange buffer
+// [component][even/odd][m][line], m in [0, M), reused by both exchanges (the
+// middle phase reads all of it before any thread overwrites it).
+template <int R2, int NL>
+__global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
     using C = float2;
-    constexpr int M = 16 * R2, L3 = 2 * M;
-    constexpr size_t XB = (size_t)6 * M * NL;   // one exchange buffer
+    constexpr int M = 16 * R2, L3 = 2 * M, NT = 32 * NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
-    C* exf = tw + L3;
-    C* exi = exf + XB;
+    C* ex = tw + L3;
     const int k10 = blockIdx.x * NL, j = blockIdx.z;
     // visit k2 and its mirror L2 - k2 back to back (they share spectrum octants)
     const int y = blockIdx.y;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(NT) k_zreg(ConvArgs<float> a) {
         }
         dftR<false>(e, int_<16>());
         dftR<false>(o, int_<16>());
-        C* de = exf + (size_t)(comp * 2) * M * NL + l;
+        C* de = ex + (size_t)(comp * 2) * M * NL + l;
         C* dodd = de + (size_t)M * NL;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -293,34 +293,39 @@ __global__ void __launch_bounds__(NT) k_zreg(ConvArgs<float> a) {
         }
     }
     __syncthreads();
-    // forward stage B, spectrum multiply, inverse stage A: one (half, k1, line) per item
-    const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
-    const int kk2 = k2 <= a.L2 / 2 ? k2 : a.L2 - k2;
-    const float sg2 = k2 <= a.L2 / 2 ? 1.f : -1.f;
-    for (int w = threadIdx.x; w < 32 * NL; w += NT) {
+    // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line)
+    {
+        const int w = threadIdx.x;
         const int l = w % NL, k1 = (w / NL) % 16, half = w / (16 * NL);
         const int k1g = k10 + l;
         C v[3][R2];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const C* src = exf + (size_t)(c * 2 + half) * M * NL + l;
+            const C* src = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
             for (int t = 0; t < R2; ++t) v[c][t] = src[(t * 16 + k1) * NL];
-            dftR<false>(v[c], int_<R2>());     // v[c][q]: frequency 2 (k1 + 16 q) + half
         }
+        __syncthreads();   // every item has read its inputs; the buffer is reused below
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dftR<false>(v[c], int_<R2>());   // v[c][q]: frequency 2 (k1 + 16 q) + half
         if (k1g < a.L1) {
+            const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
+            const int kk2 = k2 <= a.L2 / 2 ? k2 : a.L2 - k2;
+            const float sg2 = k2 <= a.L2 / 2 ? 1.f : -1.f;
             const int kk1 = k1g <= a.L1 / 2 ? k1g : a.L1 - k1g;
             const float sg1 = k1g <= a.L1 / 2 ? 1.f : -1.f;
+            const C* sp = a.spec + kk1 + (size_t)a.Lh1 * kk2;
+            const size_t st3 = (size_t)a.Lh1 * a.Lh2;
 #pragma unroll
             for (int q = 0; q < R2; ++q) {
                 const int k3 = 2 * (k1 + 16 * q) + half;
                 const int kk3 = k3 <= L3 / 2 ? k3 : L3 - k3;
                 const float sg3 = k3 <= L3 / 2 ? 1.f : -1.f;
-                const size_t o = kk1 + (size_t)a.Lh1 * (kk2 + (size_t)a.Lh2 * kk3);
-                const C txx = a.spec[o], tyy = a.spec[oct + o], tzz = a.spec[2 * oct + o];
-                const C txy = cscale(a.spec[3 * oct + o], sg1 * sg2);
-                const C txz = cscale(a.spec[4 * oct + o], sg1 * sg3);
-                const C tyz = cscale(a.spec[5 * oct + o], sg2 * sg3);
+                const C* so = sp + st3 * kk3;
+                const C txx = so[0], tyy = so[oct], tzz = so[2 * oct];
+                const C txy = cscale(so[3 * oct], sg1 * sg2);
+                const C txz = cscale(so[4 * oct], sg1 * sg3);
+                const C tyz = cscale(so[5 * oct], sg2 * sg3);
                 const C x = v[0][q], yv = v[1][q], z = v[2][q];
                 C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
                 cfma(ox, txy, yv); cfma(ox, txz, z);
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(NT) k_zreg(ConvArgs<float> a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             dftR<true>(v[c], int_<R2>());      // v[c][n1] = sum_q X[k1 + 16 q] w_R2^(-q n1)
-            C* dst = exi + (size_t)(c * 2 + half) * M * NL + l;
+            C* dst = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
             for (int n1 = 0; n1 < R2; ++n1)
                 dst[(k1 * R2 + n1) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(NT) k_zreg(ConvArgs<float> a) {
         const int l = w % NL, n1 = (w / NL) % R2, comp = w / (NL * R2);
         const int k1g = k10 + l;
         C e[16], o[16];
-        const C* se = exi + (size_t)(comp * 2) * M * NL + l;
+        const C* se = ex + (size_t)(comp * 2) * M * NL + l;
         const C* so = se + (size_t)M * NL;
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {

@@ -6,8 +6,9 @@
 // the inverse diagonal of the body block, h^3 (1/chi - self term), on material
 // voxels (identity on vacuum voxels).
 //
-// Set-up: Z_nn is read off this context's own FP32 matvec applied to unit
-// vectors on the near unknowns; both blocks are inverted once in FP32 by LU
+// Set-up: Z_nn is the direct near block when vsie_setup provides it, else it is
+// read off this context's own FP32 matvec applied to unit vectors on the near
+// unknowns; both blocks are inverted once in FP32 by LU
 // (cuSOLVER getrf/getrs, set-up only).  The FP64 copies used by the FP64 solver
 // are the widened FP32 inverses (M only has to be a fixed operator).
 // Application (every GMRES iteration): two dense complex GEMMs and one
@@ -115,7 +116,22 @@ void build_block_precond(Ctx& c) {
         VSIE_CUDA(cudaGetLastError());
         c.f32.pc_Zffi = to_panel(c, A, c.m_f, c.m_f);   // frees A
     }
-    if (c.m_n > 0) {
+    if (c.m_n > 0 && c.hZnn_direct.size() == (size_t)c.m_n * c.m_n) {
+        // the set-up's direct near block Z_nn = -K_nn: the near-near block of the
+        // operator (the grid part folded out of Znn~ is added back by the grid)
+        const size_t nn = (size_t)c.m_n * c.m_n;
+        std::vector<float2> h32(nn);
+        for (size_t i = 0; i < nn; ++i)
+            h32[i] = make_float2((float)c.hZnn_direct[i].real(), (float)c.hZnn_direct[i].imag());
+        std::vector<std::complex<double>>().swap(c.hZnn_direct);
+        float2* A = (float2*)dalloc(c, nn * sizeof(float2));
+        VSIE_CUDA(cudaMemcpy(A, h32.data(), nn * sizeof(float2), cudaMemcpyHostToDevice));
+        invert_f32(c, A, c.m_n);
+        c.f32.pc_Znni = A;
+        c.f64.pc_Znni = (double2*)dalloc(c, nn * sizeof(double2));
+        k_f32_widen<<<2048, 256>>>(A, c.f64.pc_Znni, nn);
+        VSIE_CUDA(cudaGetLastError());
+    } else if (c.m_n > 0) {
         const int mn = c.m_n;
         const size_t nn = (size_t)mn * mn;
         float2* A = (float2*)dalloc(c, nn * sizeof(float2));

@@ -550,6 +550,7 @@ static std::vector<cd> to_host(const double2* d, size_t n) {
 // ------------------------------------------------------------------ set-up driver
 struct Built {
     std::vector<cd> W, pre_val, Znn, U, V, tt[3][4];
+    std::vector<cd> Znn_direct;   // Z_nn = -K_nn itself (the near-near block of the operator)
     std::vector<int32_t> base, pre_col;
     std::vector<int64_t> pre_row;
     int aca_rank = 0;
@@ -720,52 +721,19 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         }
 
         T.mark("precorrection");
-        // --- direct near block and the grid part P^T K P
+        // --- direct near block and the grid part P^T K P: Znn~ = Z_nn - (-h^3 P^T T P),
+        // the grid part summed directly over stencil pairs (it equals the grid
+        // convolution exactly; see ptkp_add)
         double2* Knn = (double2*)dalloc(S.c, (size_t)m_n * m_n * sizeof(double2));
         efie_block(md_c, md_c, true, m_n, nullptr, m_n, nullptr, k0, -1.0, Knn, m_n);
-        std::vector<cd> Znn = to_host(Knn, (size_t)m_n * m_n);
+        B.Znn_direct = to_host(Knn, (size_t)m_n * m_n);
         {
-            vsie_options to = o;
-            to.precisions = 1 << VSIE_C128;
-            to.max_rhs = std::min(m_n, 16);
-            std::vector<cd> zeros((size_t)m_n * m_n, 0.0);
-            vsie_parts pp{};
-            pp.m_n = m_n;
-            pp.stencil = s;
-            pp.W = reinterpret_cast<const double*>(B.W.data());
-            pp.base = B.base.data();
-            pp.Znn = reinterpret_cast<const double*>(zeros.data());
-            Ctx* tc = nullptr;
-            vsie_status st = create_from_parts_impl(body, eps_r, sigma, freq, &to, &pp, nullptr, &tc);
-            if (st != VSIE_OK) throw Error(st, "grid context for the near block failed");
-            try {
-                const int p = to.max_rhs;
-                const int64_t N = tc->N;
-                double2* Xd = (double2*)dalloc(S.c, (size_t)N * p * sizeof(double2));
-                double2* Yd = (double2*)dalloc(S.c, (size_t)N * p * sizeof(double2));
-                double2* Ptkp = (double2*)dalloc(S.c, (size_t)m_n * m_n * sizeof(double2));
-                for (int c0 = 0; c0 < m_n; c0 += p) {
-                    const int pc = std::min(p, m_n - c0);
-                    VSIE_CUDA(cudaMemset(Xd, 0, (size_t)N * p * sizeof(double2)));
-                    for (int j = 0; j < pc; ++j) {
-                        const double2 e1 = one;
-                        VSIE_CUDA(cudaMemcpy(Xd + (size_t)N * j + c0 + j, &e1, sizeof(double2),
-                                             cudaMemcpyHostToDevice));
-                    }
-                    matvec_internal<double>(*tc, pc, Xd, N, Yd, N, 0);
-                    VSIE_CUDA(cudaMemcpy2D(Ptkp + (size_t)m_n * c0, m_n * sizeof(double2), Yd,
-                                           N * sizeof(double2), m_n * sizeof(double2), pc,
-                                           cudaMemcpyDeviceToDevice));
-                }
-                // y_n = -P^T K P e;  Znn~ = Z_nn(direct) - y_n
-                const std::vector<cd> y = to_host(Ptkp, (size_t)m_n * m_n);
-                for (size_t i = 0; i < Znn.size(); ++i) Znn[i] -= y[i];
-            } catch (...) {
-                destroy_ctx(tc);
-                throw;
-            }
-            destroy_ctx(tc);
+            int* dbase = up(S.c, B.base);
+            const double a = std::cbrt(3.0 / (4.0 * M_PI)) * h;
+            const cd sv = (2.0 / 3.0) * cd(1.0, k0 * a) * std::exp(cd(0.0, -k0 * a)) - 1.0;
+            ptkp_add(m_n, s, dW, dbase, h, k0, d2(sv), Knn, m_n);
         }
+        std::vector<cd> Znn = to_host(Knn, (size_t)m_n * m_n);
         B.Znn = std::move(Znn);
         T.mark("near block");
     }
@@ -860,14 +828,15 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             cgemm2<double>(L.c, OP_H, OP_H, m_f, k, k, one, Ra, k, 0, Sk, k, 0, zero, Vall, m_f, 0, 1,
                            nullptr, nullptr, 0);
             T.mark("TT skeleton");
-            // orthonormalise V (m_f x k) by Cholesky QR, twice: V = Q R; U' = U R^H
-            double2* Vd = (double2*)dalloc(L.c, (size_t)m_f * k * sizeof(double2));
-            VSIE_CUDA(cudaMemcpy(Vd, Vall, (size_t)m_f * k * sizeof(double2), cudaMemcpyDeviceToDevice));
-            double2* Up = (double2*)dalloc(L.c, (size_t)n_b * k * sizeof(double2));
-            VSIE_CUDA(cudaMemcpy(Up, Ud, (size_t)n_b * k * sizeof(double2), cudaMemcpyDeviceToDevice));
+            // orthonormalise V (m_f x k) by Cholesky QR, twice: V = Q R; U' = U R^H.
+            // U' overwrites Z[:, J] in place, in row chunks (n_b k values of FP64
+            // complex are ~40 GB at the 1 mm head grid: no second copy is made)
+            double2* Vd = Vall;
+            double2* Up = Ud;
+            const int64_t chunk = std::min<int64_t>(n_b, std::max<int64_t>(m_f, (int64_t)1 << 20));
             double2* Gk = (double2*)dalloc(L.c, (size_t)k * k * sizeof(double2));
             double2* Rk = (double2*)dalloc(L.c, (size_t)k * k * sizeof(double2));
-            double2* Tq = (double2*)dalloc(L.c, (size_t)std::max<int64_t>(m_f, n_b) * k * sizeof(double2));
+            double2* Tq = (double2*)dalloc(L.c, (size_t)std::max<int64_t>(chunk, m_f) * k * sizeof(double2));
             for (int pass = 0; pass < 2; ++pass) {
                 cgemm<double>(L.c, OP_H, k, k, m_f, one, Vd, m_f, 0, Vd, m_f, 0, zero, Gk, k, 0, 1, nullptr, nullptr, 0);
                 std::vector<cd> G = to_host(Gk, (size_t)k * k);
@@ -886,8 +855,13 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
                 cgemm<double>(L.c, OP_N, m_f, k, k, one, Vd, m_f, 0, Rk, k, 0, zero, Tq, m_f, 0, 1, nullptr, nullptr, 0);
                 VSIE_CUDA(cudaMemcpy(Vd, Tq, (size_t)m_f * k * sizeof(double2), cudaMemcpyDeviceToDevice));
                 VSIE_CUDA(cudaMemcpy(Rk, hr.data(), hr.size() * sizeof(double2), cudaMemcpyHostToDevice));
-                cgemm2<double>(L.c, OP_N, OP_H, (int)n_b, k, k, one, Up, n_b, 0, Rk, k, 0, zero, Tq, n_b, 0, 1, nullptr, nullptr, 0);
-                VSIE_CUDA(cudaMemcpy(Up, Tq, (size_t)n_b * k * sizeof(double2), cudaMemcpyDeviceToDevice));
+                for (int64_t r0 = 0; r0 < n_b; r0 += chunk) {
+                    const int rows = (int)std::min<int64_t>(chunk, n_b - r0);
+                    cgemm2<double>(L.c, OP_N, OP_H, rows, k, k, one, Up + r0, n_b, 0, Rk, k, 0, zero, Tq, rows, 0, 1,
+                                   nullptr, nullptr, 0);
+                    VSIE_CUDA(cudaMemcpy2D(Up + r0, n_b * sizeof(double2), Tq, rows * sizeof(double2),
+                                           rows * sizeof(double2), k, cudaMemcpyDeviceToDevice));
+                }
             }
             // truncated TT-SVD of U' over (n1, n2, n3, k)
             const double tot = frob2(L, Up, n_b * k);
@@ -952,6 +926,7 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         al.erase(std::remove(al.begin(), al.end(), (void*)B.dZff), al.end());
         c->allocs.push_back(B.dZff);
     }
+    c->hZnn_direct = std::move(B.Znn_direct);
     if (c->f32.ready && c->f64.ready) {
         try {
             build_block_precond(*c);

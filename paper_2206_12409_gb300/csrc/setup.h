@@ -51,6 +51,9 @@ void field_points(const MeshDev& m, int np, const double* pts, int nc, const int
                   const double* ctr, double k0, double2* out);
 // out[m] = scale \int f_m . e0 exp(-i k0 khat . r) dS for m RWG functions
 // described by geo (26 doubles each: see k_pw_surface)
+// Z[m + ldz n] += h^3 (P^T T P)[m, n] for the mn near RWG (direct stencil-pair sum)
+void ptkp_add(int mn, int s, const double2* W, const int* base, double h, double k0, double2 selfv, double2* Z,
+              int64_t ldz);
 void planewave_surface(int m, const double* geo, const double khat[3], const double e0[3], double k0,
                        double2 scale, double2* out, cudaStream_t st);
 

@@ -215,6 +215,7 @@ struct Ctx {
                                        // (26 doubles); set by vsie_setup, else null
     vsie_parts parts_view{};           // filled by vsie_get_parts
     std::vector<std::complex<double>> hZff_copy;
+    std::vector<std::complex<double>> hZnn_direct;   // set-up only: Z_nn for the preconditioner
 };
 
 // RAII scope charging kernel launches to a profiling group.
