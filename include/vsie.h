@@ -14,7 +14,8 @@
  * near conductors (coils) j_n, body polarisation currents j_b.  Z_bb and the
  * near block are applied by the precorrected FFT on an extended voxel grid
  * (Sec. II.C, III), Z_fn by its ACA factors U V^H (Sec. III), the far coupling
- * Z_fb by its tensor trains with Eq. (mvp) and Eq. (tmvp), and Z_ff densely.
+ * Z_fb by its tensor trains with Eq. (mvp) and Eq. (tmvp), and Z_ff densely or
+ * as a hierarchical matrix whose admissible blocks are ACA factors (Sec. II.B).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -96,6 +97,10 @@ typedef struct {
     double aca_tol;        /* ACA tolerance of the near-far block (default 1e-6)        */
     int32_t max_rhs;       /* largest p passed to vsie_matvec / vsie_solve (default 16) */
     int32_t precisions;    /* bit mask (1 << VSIE_C128) | (1 << VSIE_C64); default both */
+    int32_t far_hmatrix;   /* far-far block Z_ff (vsie_setup only): 0 = hierarchical when
+                              m_f >= 8192, else dense; 1 = hierarchical; -1 = dense     */
+    int32_t hm_leaf;       /* H-matrix leaf cluster size, <= 256 (default 128)          */
+    double hm_eta;         /* H-matrix admissibility min(diam) <= eta dist (default 1)  */
 } vsie_options;
 
 /* Compressed operator parts, for vsie_create.  All arrays are host memory,
@@ -162,9 +167,13 @@ VSIE_API const char* vsie_version(void);
  * (eps_r, sigma: n_b host doubles each, S/m), near conductors `coil` and far
  * conductors `shield` (either may be NULL), frequency in Hz.  Builds RWG
  * functions, the Green spectra of the extended grid, the pFFT projection and
- * precorrection, the dense near block, the ACA factors of Z_fn, the dense Z_ff
- * and the TT of Z_fb (ACA matrix cross over the (voxel | far RWG) unfolding,
- * then TT-SVD of the voxel factor).  Synchronous; uses the current device.
+ * precorrection, the dense near block, the ACA factors of Z_fn, Z_ff (dense, or
+ * hierarchical with ACA blocks at aca_tol: see far_hmatrix) and the TT of Z_fb
+ * (ACA matrix cross over the (voxel | far RWG) unfolding, then TT-SVD of the
+ * voxel factor).  With a hierarchical Z_ff the dense block is kept only while
+ * the preconditioner is built: vsie_get_parts and vsie_save then return
+ * EUNSUPPORTED, and plain FP64 solves (mode 0, which need the FP64 inverse of
+ * the dense block) return EUNSUPPORTED.  Synchronous; uses the current device.
  * Returns EINVAL for malformed meshes/grids or stencils leaving the extended
  * grid, ENOMEM/ECUDA on device failures.  *out is set only on success. */
 VSIE_API vsie_status vsie_setup(const vsie_grid* body, const double* eps_r, const double* sigma,

@@ -469,6 +469,8 @@ void destroy_ctx(Ctx* c) {
 // vsie_get_parts: host views of the operator parts (Zff copied from the device
 // when the set-up produced it there).
 static void fill_parts(Ctx& c, vsie_parts& p) {
+    if (c.hm.on)
+        throw Error(VSIE_EUNSUPPORTED, "the far-far block is hierarchical; its dense form is not kept");
     p = vsie_parts{};
     p.m_f = c.m_f;
     p.m_n = c.m_n;

@@ -109,11 +109,14 @@ void build_block_precond(Ctx& c) {
     if (c.m_f > 0) {
         const size_t nn = (size_t)c.m_f * c.m_f;
         float2* A = (float2*)dalloc(c, nn * sizeof(float2));
+        if (!c.f32.Zff) throw Error(VSIE_EUNSUPPORTED, "the dense far-far block is no longer held");
         from_panel(c.f32.Zff, c.m_f, c.m_f, A);     // the FP32 Z_ff is stored in row panels
         invert_f32(c, A, c.m_f);
-        c.f64.pc_Zffi = (double2*)dalloc(c, nn * sizeof(double2));
-        k_f32_widen<<<2048, 256>>>(A, c.f64.pc_Zffi, nn);
-        VSIE_CUDA(cudaGetLastError());
+        if (!c.hm.on) {   // with the hierarchical block only the FP32 (mixed) solves apply it
+            c.f64.pc_Zffi = (double2*)dalloc(c, nn * sizeof(double2));
+            k_f32_widen<<<2048, 256>>>(A, c.f64.pc_Zffi, nn);
+            VSIE_CUDA(cudaGetLastError());
+        }
         c.f32.pc_Zffi = to_panel(c, A, c.m_f, c.m_f);   // frees A
     }
     if (c.m_n > 0 && c.hZnn_direct.size() == (size_t)c.m_n * c.m_n) {
@@ -194,6 +197,8 @@ void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, i
     prof_count(c, 1);
     const cx<R> one = mk<cx<R>>(1, 0), zero = mk<cx<R>>(0, 0);
     if (c.m_f > 0) {
+        if (!d.pc_Zffi)
+            throw Error(VSIE_EUNSUPPORTED, "no FP64 far-block inverse (hierarchical Z_ff): use the mixed solve");
         if constexpr (sizeof(R) == 4)
             gemm_panel(c, c.m_f, p, c.m_f, d.pc_Zffi, X, ldx, Y, ldy, st);   // FP32: row panels
         else

@@ -15,6 +15,7 @@
 //    truncated TT-SVD of the voxel factor over (n1, n2, n3, k) (Sec. II.D).
 #include "setup.h"
 #include "hostla.h"
+#include "hmatrix.h"
 
 #include <cusolverDn.h>
 
@@ -927,6 +928,37 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
         c->allocs.push_back(B.dZff);
     }
     c->hZnn_direct = std::move(B.Znn_direct);
+    // hierarchical far-far block: cluster tree over the far RWG functions (centres:
+    // midpoints of the two triangle centroids; supports: boxes of both triangles)
+    const bool want_hm = has_s && c->f32.ready && c->f64.ready &&
+                         (o.far_hmatrix > 0 || (o.far_hmatrix == 0 && m_f >= 8192));
+    if (want_hm) {
+        try {
+            std::vector<double> cen(3 * (size_t)m_f), slo(3 * (size_t)m_f), shi(3 * (size_t)m_f);
+            for (int i = 0; i < m_f; ++i) {
+                for (int d = 0; d < 3; ++d) {
+                    cen[3 * i + d] = 0.5 * (mh_s.centroid[3 * mh_s.tplus[i] + d] + mh_s.centroid[3 * mh_s.tminus[i] + d]);
+                    slo[3 * i + d] = 1e300;
+                    shi[3 * i + d] = -1e300;
+                }
+                for (int t : {mh_s.tplus[i], mh_s.tminus[i]})
+                    for (int k = 0; k < 3; ++k)
+                        for (int d = 0; d < 3; ++d) {
+                            const double x = mh_s.xyz[3 * (size_t)mh_s.tri[3 * t + k] + d];
+                            slo[3 * i + d] = std::min(slo[3 * i + d], x);
+                            shi[3 * i + d] = std::max(shi[3 * i + d], x);
+                        }
+            }
+            const int leaf = o.hm_leaf > 0 ? std::min(o.hm_leaf, 256) : 128;
+            const double eta = o.hm_eta > 0 ? o.hm_eta : 1.0;
+            const HmPlan plan = hm_plan(m_f, cen.data(), slo.data(), shi.data(), leaf, eta);
+            hm_build(*c, plan, B.dZff, m_f, aca_tol);
+        } catch (...) {
+            destroy_ctx(c);
+            throw;
+        }
+        T.mark("far-far H-matrix");
+    }
     if (c->f32.ready && c->f64.ready) {
         try {
             build_block_precond(*c);
@@ -935,6 +967,20 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             throw;
         }
         T.mark("block preconditioner");
+    }
+    if (c->hm.on) {
+        // the dense far-far block (FP64, and its FP32 panels) served the ACA and the
+        // preconditioner's factorisation; the product uses the H-matrix from now on
+        auto release = [&](void* ptr) {
+            auto& al = c->allocs;
+            al.erase(std::remove(al.begin(), al.end(), ptr), al.end());
+            cudaFree(ptr);
+        };
+        release(c->f32.Zff);
+        release(c->f64.Zff);
+        c->f32.Zff = nullptr;
+        c->f64.Zff = nullptr;
+        c->dZff_in = nullptr;
     }
     // RWG geometry for the plane-wave right-hand side (far first, then near)
     {

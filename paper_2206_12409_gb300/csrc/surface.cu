@@ -8,8 +8,9 @@
 //       Eq. (tmvp), each a chain of contractions: the first core against the
 //       body by k_tt_g1 / k_tt_g1t (masked, all RHS in one launch), the others
 //       by the GEMM kernels of gemm.cu.
-// The FP32 Z_ff is stored in row panels and applied by gemm_panel.
-#include "vsie_internal.h"
+// The FP32 dense Z_ff is stored in row panels and applied by gemm_panel; a
+// hierarchical Z_ff (hmatrix.cu) replaces both dense products.
+#include "hmatrix.h"
 
 namespace vsie {
 
@@ -199,7 +200,9 @@ void surface_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t
     if (mf > 0) {
         {
         ProfScope ps(c, PG_SURF, st);
-        if constexpr (sizeof(R) == 4)
+        if (c.hm.on)
+            hm_apply<R>(c, p, X, ldx, Y, ldy, st);                    // hierarchical Z_ff
+        else if constexpr (sizeof(R) == 4)
             gemm_panel(c, mf, p, mf, d.Zff, X, ldx, Y, ldy, st);   // FP32 Z_ff in row panels
         else
             cgemm<R>(c, OP_N, mf, p, mf, one, d.Zff, mf, 0, X, ldx, 0, zero, Y, ldy, 0, 1, nullptr,

@@ -142,8 +142,29 @@ struct Prof {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PG_N];
 };
 
+// Hierarchical far-far block (hmatrix.cu): index structures and data, device.
+struct HmDev {
+    bool on = false;
+    int m = 0, nrl = 0, nblk = 0, nlr = 0, nt = 0, ndense = 0;
+    int64_t nD = 0, nU = 0, nV = 0;
+    int* perm = nullptr;       // cluster position -> RWG index
+    int* rl = nullptr;         // leaf row clusters (nrl + 1)
+    int4* blk = nullptr;       // (row start, rows, column start, columns) per block
+    int* kb = nullptr;         // rank per block, -1 dense
+    int64_t* doff = nullptr;   // dense: offset in D; low rank: offset of U
+    int64_t* voff = nullptr;   // low rank: offset of V
+    int* toff = nullptr;       // low rank: first row of t
+    int* lr = nullptr;         // low-rank blocks with rank > 0
+    int* eptr = nullptr;       // per leaf row cluster: blocks covering it (CSR)
+    int* eblk = nullptr;
+    int* eroff = nullptr;      // row offset of the leaf inside the block
+    double2 *D64 = nullptr, *U64 = nullptr, *V64 = nullptr, *xt64 = nullptr, *t64 = nullptr;
+    float2 *D32 = nullptr, *U32 = nullptr, *V32 = nullptr, *xt32 = nullptr, *t32 = nullptr;
+};
+
 struct Ctx {
     std::string err;
+    HmDev hm;
     Prof prof;
     int device = 0;
     // problem

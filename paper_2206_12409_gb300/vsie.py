@@ -53,7 +53,8 @@ class vsie_mesh(C.Structure):
 class vsie_options(C.Structure):
     _fields_ = [("ext_n", C.c_int32 * 3), ("ext_offset", C.c_int32 * 3), ("stencil", C.c_int32),
                 ("near_radius", C.c_int32), ("colloc_rfac", C.c_double), ("tt_tol", C.c_double),
-                ("aca_tol", C.c_double), ("max_rhs", C.c_int32), ("precisions", C.c_int32)]
+                ("aca_tol", C.c_double), ("max_rhs", C.c_int32), ("precisions", C.c_int32),
+                ("far_hmatrix", C.c_int32), ("hm_leaf", C.c_int32), ("hm_eta", C.c_double)]
 
 
 class vsie_parts(C.Structure):
@@ -195,7 +196,8 @@ def make_mesh(xyz, tri, ports=None):
 
 
 def make_options(ext_n=None, ext_offset=None, stencil=0, near_radius=0, colloc_rfac=0.0,
-                 tt_tol=0.0, aca_tol=0.0, max_rhs=0, precisions=0):
+                 tt_tol=0.0, aca_tol=0.0, max_rhs=0, precisions=0, far_hmatrix=0, hm_leaf=0,
+                 hm_eta=0.0):
     o = vsie_options()
     for i in range(3):
         o.ext_n[i] = int(ext_n[i]) if ext_n is not None else 0
@@ -203,6 +205,7 @@ def make_options(ext_n=None, ext_offset=None, stencil=0, near_radius=0, colloc_r
     o.stencil, o.near_radius, o.colloc_rfac = int(stencil), int(near_radius), float(colloc_rfac)
     o.tt_tol, o.aca_tol, o.max_rhs, o.precisions = float(tt_tol), float(aca_tol), int(max_rhs), \
         int(precisions)
+    o.far_hmatrix, o.hm_leaf, o.hm_eta = int(far_hmatrix), int(hm_leaf), float(hm_eta)
     return o
 
 
@@ -408,7 +411,7 @@ def parts_to_numpy(ctx, body_n):
     return out
 
 
-def setup_problem(prob, max_rhs=8, precisions=0):
+def setup_problem(prob, max_rhs=8, precisions=0, far_hmatrix=0, hm_leaf=0, hm_eta=0.0):
     """vsie_setup for an inputs.Problem (geometry marshalling only)."""
     g = prob.grid
     coil = shield = None
@@ -421,7 +424,8 @@ def setup_problem(prob, max_rhs=8, precisions=0):
         keep.append(k2)
     opts = make_options(ext_n=prob.ext_n, ext_offset=prob.ext_offset, stencil=prob.stencil,
                         tt_tol=prob.tt_tol, aca_tol=prob.aca_tol, max_rhs=max_rhs,
-                        precisions=precisions)
+                        precisions=precisions, far_hmatrix=far_hmatrix, hm_leaf=hm_leaf,
+                        hm_eta=hm_eta)
     return vsie_setup(make_grid(g.n, g.h, g.origin), prob.eps_r, prob.sigma, coil, shield,
                       prob.freq_hz, opts)
 
