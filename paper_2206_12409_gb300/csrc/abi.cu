@@ -94,7 +94,7 @@ static cx<R>* up_c(Ctx& c, const std::vector<std::complex<double>>& h) {
 // [chunk][3][n3][L2][L1] complex values.  The right-hand sides of one matvec are
 // processed in groups of `chunk` so that the buffers stay within kConvWorkBudget
 // bytes (a 1 mm head grid needs 2.1 GB per FP32 right-hand side).
-constexpr size_t kConvWorkBudget = 24ull << 30;
+constexpr size_t kConvWorkBudget = 16ull << 30;
 
 static size_t conv_elems_A(const Ctx& c) { return 3 * (size_t)c.ne[2] * c.ne[1] * c.L[0]; }
 static size_t conv_elems_B(const Ctx& c) { return 3 * (size_t)c.ne[2] * c.L[1] * c.L[0]; }

@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <functional>
 #include <numeric>
 
@@ -582,6 +584,15 @@ void hm_build(Ctx& c, const HmPlan& P, const double2* dZ, int64_t ldz, double to
     H.ndense = (int)dense_ids.size();
     VSIE_CUDA(cudaDeviceSynchronize());
     H.on = true;
+    if (std::getenv("VSIE_TRACE")) {
+        int kmax = 0, nfall = 0;
+        for (int b = 0; b < nb; ++b) kmax = std::max(kmax, kb[b]);
+        for (int b : lr_try) nfall += kb[b] < 0;
+        fprintf(stderr, "[vsie H] m %d leaves %d blocks %d (dense %d, low rank %d, ACA fallbacks %d) max rank %d, "
+                        "%.3f GB FP64 data (dense-block equivalent %.3f GB)\n",
+                P.m, H.nrl, nb, H.ndense, H.nlr, nfall, kmax, (nD + nU + nV) * 16.0 / 1e9,
+                (double)P.m * P.m * 16.0 / 1e9);
+    }
 }
 
 template <typename R>

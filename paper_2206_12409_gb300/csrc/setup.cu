@@ -26,24 +26,26 @@
 #include <chrono>
 #include <cstdio>
 #include <random>
+#include <cstdlib>
 
 namespace vsie {
 
 using hla::cd;
 
-// Phase timing of the set-up, printed to stderr when built with -DVSIE_TRACE.
+// Phase timing of the set-up, printed to stderr when the environment variable
+// VSIE_TRACE is set.
 struct PhaseTimer {
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    const bool on = std::getenv("VSIE_TRACE") != nullptr;
     void mark(const char* what) {
-#ifdef VSIE_TRACE
+        if (!on) return;
         cudaDeviceSynchronize();
         const auto t = std::chrono::steady_clock::now();
-        fprintf(stderr, "[vsie setup] %-28s %8.3f s\n", what,
-                std::chrono::duration<double>(t - t0).count());
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        fprintf(stderr, "[vsie setup] %-28s %8.3f s  (device free %.1f GB)\n", what,
+                std::chrono::duration<double>(t - t0).count(), fr / 1e9);
         t0 = t;
-#else
-        (void)what;
-#endif
     }
 };
 
@@ -911,11 +913,10 @@ static void setup_impl(const vsie_grid* body, const double* eps_r, const double*
             for (int q = 0; q < 4; ++q) P.tt_core[a][q] = reinterpret_cast<const double*>(B.tt[a][q].data());
         }
     }
-#ifdef VSIE_TRACE
-    fprintf(stderr, "[vsie setup] m_f %d m_n %d aca rank %d tt ranks %d,%d,%d | %d,%d,%d | %d,%d,%d\n", m_f, m_n,
-            P.aca_rank, P.tt_rank[0][0], P.tt_rank[0][1], P.tt_rank[0][2], P.tt_rank[1][0], P.tt_rank[1][1],
-            P.tt_rank[1][2], P.tt_rank[2][0], P.tt_rank[2][1], P.tt_rank[2][2]);
-#endif
+    if (T.on)
+        fprintf(stderr, "[vsie setup] m_f %d m_n %d aca rank %d tt ranks %d,%d,%d | %d,%d,%d | %d,%d,%d\n", m_f, m_n,
+                P.aca_rank, P.tt_rank[0][0], P.tt_rank[0][1], P.tt_rank[0][2], P.tt_rank[1][0], P.tt_rank[1][1],
+                P.tt_rank[1][2], P.tt_rank[2][0], P.tt_rank[2][1], P.tt_rank[2][2]);
     vsie_options fo = o;
     fo.stencil = s;
     Ctx* c = nullptr;

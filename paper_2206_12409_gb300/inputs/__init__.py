@@ -25,7 +25,7 @@ __all__ = [
     "sphere_phantom", "layered_head_phantom",
     "loop_strip", "closed_cylinder", "open_cylinder", "loop_array_on_cylinder",
     "merge_meshes", "random_vectors", "problem_sphere_loop_shield",
-    "problem_head", "problem_volume_only", "problem_coil_array_mid",
+    "problem_head", "problem_volume_only", "problem_coil_array_mid", "problem_head_1mm",
 ]
 
 
@@ -395,3 +395,15 @@ def problem_coil_array_mid(n_body=(18, 18, 24), h=5e-3, freq_hz=298e6, ext_n=(26
     off = tuple((e - b) // 2 for e, b in zip(ext_n, n_body))
     return Problem("coil_array_mid", g, er, sg, freq_hz, coil, shield, tuple(ext_n), off, 3,
                    tt_tol, aca_tol, nrhs)
+
+
+def problem_head_1mm(freq_hz=298e6, seed=0, nrhs=16):
+    """Head at 1 mm: the layered ellipsoid family of problem_head on a
+    192 x 192 x 224 grid (the same 192 x 192 x 224 mm box; 2.48e7 body unknowns),
+    a 16-loop strip array on the 0.12 m cylinder (512 triangles per loop, 8192 in
+    all, 16 ports) on the 256 x 256 x 224 extended grid, and the shield/bore
+    cylinder r = 0.33 m, L = 1.2 m of 40,000 triangles (200 x 100 quads); TT and
+    ACA tolerance 1e-5; one right-hand side per port."""
+    return problem_head(n_body=(192, 192, 224), h=1e-3, freq_hz=freq_hz, ext_n=(256, 256, 224),
+                        n_loops=16, loop_seg=256, shield_theta=200, shield_z=100, tt_tol=1e-5,
+                        aca_tol=1e-5, seed=seed, nrhs=nrhs)
