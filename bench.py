@@ -1,21 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark of the hybrid-VSIE solve on one GB300 (or N independent replicas).
+"""Benchmark of the hybrid-VSIE operator and its GMRES on one GB300 (or N
+independent replicas).
 
-Workload (head-size, 8-RHS batched): 96 x 96 x 112 voxel grid at 2 mm holding a
-3-tissue layered ellipsoid head phantom with a seeded 3 mm RMS boundary
-perturbation, an 8-loop strip array (4096 triangles) coupled by pFFT (3^3
-stencil), a shield/bore cylinder r = 0.33 m, L = 1.2 m (20000 triangles) coupled
-by the TT cross at 1e-5, 298 MHz.
+Workload (the largest single-GPU configuration): head at 1 mm, a 192 x 192 x 224
+voxel grid holding the 3-tissue layered ellipsoid head phantom with a seeded 3 mm
+RMS boundary perturbation (2.48e7 body unknowns); a 16-loop strip array of 8192
+triangles coupled by pFFT (3^3 stencil) on a 256 x 256 x 224 grid (FFT lengths
+512 x 512 x 448); the shield/bore cylinder r = 0.33 m, L = 1.2 m of 40,000
+triangles (59,800 RWG functions) coupled by the TT cross at 1e-5, its own block a
+hierarchical matrix with ACA blocks at 1e-5; 298 MHz; 16 port right-hand sides.
+The set-up (assembly and compression) is outside every timed region.
 
-Step = one solve of the 8 port right-hand sides (1 V delta gaps) to a true FP64
-relative residual of 1e-6: flexible GMRES(50) with the FP32 operator inside, FP64
-Gram-Schmidt and Givens, FP64 residual refinement, block preconditioner.  The set-up
-(operator assembly and compression) is outside the timed region.
-
-value = right-hand sides solved per second (whole job: all ranks); the JSON line
-also carries the time to 1e-6, the hybrid matvec throughput, the roofline of the
-FFT convolution (K1) measured live with the library's CUDA-event profiler, the
-clocks sampled during the timed region and the CPU oracle baseline.
+Step = one application of the FP32 hybrid-VSIE operator (the inner operator of
+the mixed GMRES: FFT convolution, pFFT projection, interpolation and
+precorrection, near block, ACA coupling, TT chains, H-matrix far block) to the
+16-column block.  value = right-hand-side matvecs per second of the whole job.
+Beside it, measured once each: the time to a true FP64 relative residual of
+1e-6 of the 16-RHS mixed solve (FP32 GMRES(50) with FP64 refinement, block
+preconditioner); the FFT convolution's roofline from the library's CUDA-event
+profiler over the timed steps; the clocks during the timed steps; the 2 mm head
+(96 x 96 x 112, 8 ports, dense far block) solved by the mixed and by the plain
+FP64 GMRES; and the CPU oracle's body operator on the same 1 mm grid.
 """
 from __future__ import annotations
 
@@ -34,13 +39,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "GMRES time-to-1e-6 residual (RHS solved/s) & hybrid matvecs/s"
-UNIT = "RHS-solves/s"
-WORKLOAD = ("head 96x96x112 @ 2 mm (3-tissue layered ellipsoid), 8-loop array 4096 tri via "
-            "pFFT s=3 on a 128x128x112 grid, shield/bore 20000 tri via TT 1e-5, 298 MHz, 8 port RHS")
-# mean inner (FP32) operator applications per right-hand side of the solve measured on this
-# workload; used only to scale the CPU oracle's per-matvec time to the solve metric
-ORACLE_MATVECS_PER_SOLVE = 380
+METRIC = "GMRES time-to-1e-6 residual & matvecs/s; FFT-conv HBM GB/s (hybrid-VSIE matvecs/s)"
+UNIT = "RHS-matvecs/s"
+WORKLOAD = ("head 192x192x224 @ 1 mm (3-tissue layered ellipsoid, 2.48e7 body unknowns), 16-loop array "
+            "8192 tri via pFFT s=3 on a 256x256x224 grid, shield/bore 40000 tri (59800 RWG) via TT 1e-5 and "
+            "an ACA H-matrix 1e-5, 298 MHz, 16 port RHS")
+P_RHS = 16
 
 
 def _peaks():
@@ -54,18 +58,18 @@ def _peaks():
 
 def _conv_source_hash():
     h = hashlib.sha256()
-    for f in ("conv.cu", "fft.cuh"):
+    for f in ("conv.cu", "conv_reg.cuh", "fft.cuh"):
         with open(os.path.join(ROOT, "paper_2206_12409_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_per_launch(p):
-    """DRAM bytes per K1 launch group (p right-hand sides) from the committed ncu
-    summary, or None when the kernel sources changed since the counters were
-    taken.  The summary holds the bytes of one right-hand side; the passes move
-    data in proportion to p."""
-    path = os.path.join(ROOT, "profiles", "fft_conv_head_grid.md")
+    """DRAM bytes per K1 launch group of p right-hand sides from the committed ncu
+    summary of the 1 mm grid, or None when the kernel sources changed since the
+    counters were taken.  The summary holds the bytes of one right-hand side; the
+    passes move data in proportion to p."""
+    path = os.path.join(ROOT, "profiles", "fft_conv_1mm_grid.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -95,7 +99,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-f", self.path],
+                                          "-lms", "100", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -149,68 +153,180 @@ def max_over_ranks(x, dist=None, device="cpu"):
 
 
 def job_value(world, rhs_per_rank, seconds):
-    """Whole-job throughput: the right-hand sides all ranks solved per second of
-    the slowest rank (weak scaling: each rank solves its own rhs_per_rank)."""
+    """Whole-job throughput: the right-hand sides all ranks processed per second
+    of the slowest rank (weak scaling: each rank has its own rhs_per_rank)."""
     return world * rhs_per_rank / seconds
 
 
-def cpu_oracle_matvec_seconds(reps=2):
-    """The oracle's FFT body operator (FP64, scipy.fft on all host cores) on the
-    workload's body grid, one RHS: seconds per application (best of reps)."""
-    import scipy.fft as sfft
-    from paper_2206_12409_gb300 import inputs as I
-    from oracle import physics, volume
-    g, er, sg = I.layered_head_phantom()
-    chi = physics.chi(er, sg, 298e6)
-    _, k0 = physics.omega_k0(298e6)
-    x = I.random_vectors(3 * g.nv, 1)
-    cores = len(os.sched_getaffinity(0))
-    with sfft.set_workers(cores):
-        spec = volume.kernel_spectra(g.n, g.h, k0)
-        best = 1e30
-        for _ in range(reps):
-            t = time.perf_counter()
-            volume.fft_matvec(g, chi, k0, x, spec=spec)
-            best = min(best, time.perf_counter() - t)
-    return best, cores
+# --------------------------------------------------------------------------- CPU oracle
+class OracleBody:
+    """The oracle's FFT body operator (FP64, scipy.fft on every host core) on the
+    1 mm head grid: the kernel spectra are built once (untimed), each call applies
+    the operator to one right-hand side.  The oracle cannot assemble the surface
+    blocks of this workload (dense EFIE of 59,800 and 8,192 RWG functions) in
+    bounded time, so its rate omits them and is an upper bound of the oracle's."""
+
+    def __init__(self):
+        import scipy.fft as sfft
+        from paper_2206_12409_gb300 import inputs as I
+        from oracle import physics, volume
+        self.sfft, self.volume = sfft, volume
+        self.cores = len(os.sched_getaffinity(0))
+        g, er, sg = I.layered_head_phantom((192, 192, 224), 1e-3)
+        self.g = g
+        self.chi = physics.chi(er, sg, 298e6)
+        _, self.k0 = physics.omega_k0(298e6)
+        self.x = I.random_vectors(3 * g.nv, 1)
+        t = time.perf_counter()
+        with sfft.set_workers(self.cores):
+            self.spec = volume.kernel_spectra(g.n, g.h, self.k0)
+        self.setup_s = time.perf_counter() - t
+
+    def apply(self):
+        t = time.perf_counter()
+        with self.sfft.set_workers(self.cores):
+            self.volume.fft_matvec(self.g, self.chi, self.k0, self.x, spec=self.spec)
+        return time.perf_counter() - t
 
 
 def run_reference(args):
+    """The oracle arm: W + K applications of the oracle's body operator on the
+    workload's grid, RHS-matvecs/s over the K timed ones."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    cores = len(os.sched_getaffinity(0))
+    ob = OracleBody()
     times = []
     for i in range(args.warmup + args.steps):
-        t, cores = cpu_oracle_matvec_seconds(reps=1)
+        t = ob.apply()
         if i >= args.warmup:
             times.append(t)
-    t_mv = statistics.mean(times)
-    t_step = t_mv * ORACLE_MATVECS_PER_SOLVE          # one RHS solve, extrapolated
+    t_step = statistics.mean(times)
     value = 1.0 / t_step
-    sample = (f"oracle FFT body-operator matvec (96x96x112, FP64, scipy.fft on {cores} cores), "
-              f"{t_mv:.2f} s each, scaled by {ORACLE_MATVECS_PER_SOLVE} operator applications per "
-              f"RHS solve; surface blocks omitted (they only add time)")
+    sample = (f"oracle FFT body operator (FP64, scipy.fft on {ob.cores} cores) on the 192x192x224 1 mm grid, "
+              f"one right-hand side per step, {t_step:.2f} s each ({args.steps} timed after {args.warmup} "
+              f"warm-up); spectra built once in {ob.setup_s:.1f} s (untimed); surface blocks omitted (their "
+              f"oracle assembly does not finish in bounded time; they only add time)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "host cores"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ob.cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# --------------------------------------------------------------------------- GPU arm
+def _cuda_time(fn, n, torch):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(n):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _solve_stats(V, ctx, p, B, X, N, opts, torch, tol=1e-6):
+    """One solve timed by CUDA events on the default stream (the library runs on it)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    st, info = V.vsie_solve(ctx, p, B.data_ptr(), N, X.data_ptr(), N, tol, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    return {"status": V.STATUS_NAMES.get(st, st), "converged": st == V.VSIE_OK, "seconds": s,
+            "rhs_solves_per_s": p / s, "max_true_relres_fp64": max(info.relres[:p]),
+            "mean_inner_iters": float(np.mean(info.iters[:p])), "fp32_matvecs": info.matvecs32,
+            "fp64_matvecs": info.matvecs64}
+
+
+def head_2mm_solves(V, I, torch, args):
+    """The 2 mm head (96 x 96 x 112, 8 ports) with a dense far block: one mixed
+    solve and one plain FP64 solve to 1e-6 (same context, same preconditioner)."""
+    prob = I.problem_head()
+    p = prob.nrhs
+    t0 = time.perf_counter()
+    ctx = V.setup_problem(prob, max_rhs=p, far_hmatrix=-1)
+    setup_s = time.perf_counter() - t0
+    try:
+        N = V.vsie_sizes(ctx)[0]
+        B = torch.zeros((p, N), dtype=torch.complex128, device="cuda")
+        V.vsie_rhs_ports(ctx, list(range(p)), 1.0, B.data_ptr(), N)
+        X = torch.zeros_like(B)
+        o = V.vsie_solve_opts()
+        o.mode, o.restart, o.maxit, o.inner_tol, o.precond = 1, 50, 3000, 1e-3, 0
+        _solve_stats(V, ctx, p, B, X, N, o, torch)          # warm-up
+        mixed = _solve_stats(V, ctx, p, B, X, N, o, torch)
+        x_mixed = X.clone()
+        out = {"workload": "head 96x96x112 @ 2 mm, 8-loop array 4096 tri, shield 20000 tri (dense far "
+                           "block), 8 port RHS", "setup_s": setup_s, "mixed": mixed}
+        if not args.no_plain:
+            o.mode = 0
+            plain = _solve_stats(V, ctx, p, B, X, N, o, torch)
+            out["plain_fp64"] = plain
+            out["plain_over_mixed_time"] = plain["seconds"] / mixed["seconds"]
+            out["solution_rel_diff"] = float((torch.linalg.norm(X - x_mixed) / torch.linalg.norm(X)).item())
+        return out
+    finally:
+        V.vsie_destroy(ctx)
+
+
+def profile_matvec(args):
+    """One FP32 body-operator matvec (K1, five FFT passes) with p right-hand sides
+    on the head grid of the chosen resolution, after three warm-up matvecs and
+    bracketed by cudaProfilerStart/Stop, so that an ncu capture started with
+    --profile-from-start off records exactly that matvec's kernels."""
+    import torch
+    from paper_2206_12409_gb300 import inputs as I
+    from paper_2206_12409_gb300 import vsie as V
+    p = args.profile_matvec
+    if args.profile_grid == "1mm":
+        g, er, sg = I.layered_head_phantom((192, 192, 224), 1e-3)
+        ext, off = (256, 256, 224), (32, 32, 0)
+    else:
+        g, er, sg = I.layered_head_phantom()
+        ext, off = (128, 128, 112), (16, 16, 0)
+    ctx = V.vsie_create(V.make_grid(g.n, g.h, g.origin), er, sg, 298e6,
+                        V.make_options(ext_n=ext, ext_offset=off, max_rhs=p, precisions=1 << V.VSIE_C64))
+    N = V.vsie_sizes(ctx)[0]
+    X = torch.randn((p, N), dtype=torch.complex64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        V.vsie_matvec(ctx, p, X.data_ptr(), N, Y.data_ptr(), N, V.VSIE_C64)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    V.vsie_matvec(ctx, p, X.data_ptr(), N, Y.data_ptr(), N, V.VSIE_C64)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    V.vsie_destroy(ctx)
+    print("profiled one matvec", args.profile_grid, "p =", p)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the timed 1 mm solve")
+    ap.add_argument("--no-head2mm", action="store_true", help="skip the 2 mm head solves")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 2 mm solve")
+    ap.add_argument("--profile-matvec", type=int, default=0, metavar="P",
+                    help="only run one bracketed FP32 body matvec with P right-hand sides (for ncu)")
+    ap.add_argument("--profile-grid", default="2mm", choices=["2mm", "1mm"])
     args = ap.parse_args()
+    if args.profile_matvec:
+        return profile_matvec(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -231,129 +347,134 @@ def main():
         torch.cuda.synchronize()
 
     # ---------------- set-up (untimed): one independent replica per rank
-    prob = I.problem_head()
-    p = prob.nrhs
+    prob = I.problem_head_1mm()
+    p = P_RHS
     t0 = time.perf_counter()
     ctx = V.setup_problem(prob, max_rhs=p)
     setup_s = time.perf_counter() - t0
     N, mf, mn, nb = V.vsie_sizes(ctx)
-    B = torch.zeros((p, N), dtype=torch.complex128, device="cuda")
-    V.vsie_rhs_ports(ctx, list(range(p)), 1.0, B.data_ptr(), N)
-    X = torch.zeros_like(B)
-    opts = V.vsie_solve_opts()
-    opts.mode, opts.restart, opts.maxit, opts.inner_tol, opts.precond = 1, 50, 3000, 1e-3, 0
+    gen = torch.Generator(device="cuda").manual_seed(12409 + rank)
+    Xm = torch.randn((p, N), dtype=torch.complex64, device="cuda", generator=gen)
+    Ym = torch.empty_like(Xm)
 
-    def solve():
-        st, info = V.vsie_solve(ctx, p, B.data_ptr(), N, X.data_ptr(), N, 1e-6, opts)
-        return st, info
+    def step():
+        V.vsie_matvec(ctx, p, Xm.data_ptr(), N, Ym.data_ptr(), N, V.VSIE_C64)
 
     for _ in range(args.warmup):
-        solve()
+        step()
     barrier()
 
-    # ---------------- timed region (device-resident inputs)
+    # ---------------- timed region: K operator applications (inputs resident in HBM)
     V.vsie_profile(ctx, 1)
     clocks = ClockSampler()
     clocks.start()
+    time.sleep(0.3)
+    barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.profiler.start()      # scope of an ncu --profile-from-start off capture
     e0.record()
-    infos = []
     for _ in range(args.steps):
-        st, info = solve()
-        infos.append((st, info))
+        step()
     e1.record()
     barrier()
-    torch.cuda.profiler.stop()
     clk = clocks.stop(local)
-    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     groups = {}
     for name, gid in V.PROFILE_GROUPS.items():
         ms, n, b = V.vsie_profile_query(ctx, gid)
         groups[name] = {"ms": ms, "launches": n, "alg_bytes": b}
     _, launches, _ = V.vsie_profile_query(ctx, -1)
     V.vsie_profile(ctx, 0)
-    ms_total = max_over_ranks(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
-    relres = max(max(info.relres[:p]) for _, info in infos)
-    conv_ok = all(st == V.VSIE_OK for st, _ in infos)
-    iters = float(np.mean([np.mean(info.iters[:p]) for _, info in infos]))
-    mv32 = float(np.mean([info.matvecs32 for _, info in infos]))
     value = job_value(world, p, ms_step / 1e3)
 
-    # ---------------- end to end: pinned host B in, X out, every step
-    Bh = B.cpu().pin_memory()
-    Xh = torch.empty_like(Bh).pin_memory()
+    # ---------------- end to end: pinned host X in, Y out, every step
+    Xh = Xm.cpu().pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        B.copy_(Bh, non_blocking=True)
-        solve()
-        Xh.copy_(X, non_blocking=True)
+        Xm.copy_(Xh, non_blocking=True)
+        step()
+        Yh.copy_(Ym, non_blocking=True)
         torch.cuda.synchronize()
     barrier()
     e2e_step = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
     e2e_value = job_value(world, p, e2e_step)
-    h2d = Bh.numel() * Bh.element_size()
-    d2h = Xh.numel() * Xh.element_size()
+    h2d = Xh.numel() * Xh.element_size()
+    d2h = Yh.numel() * Yh.element_size()
+    del Xh, Yh, Xm, Ym
+    torch.cuda.empty_cache()
 
-    # ---------------- hybrid matvec throughput (FP32 operator, 8 RHS)
-    Xm = torch.randn((p, N), dtype=torch.complex64, device="cuda")
-    Ym = torch.empty_like(Xm)
-    for _ in range(3):
-        V.vsie_matvec(ctx, p, Xm.data_ptr(), N, Ym.data_ptr(), N, V.VSIE_C64)
-    torch.cuda.synchronize()
-    m0 = torch.cuda.Event(enable_timing=True)
-    m1 = torch.cuda.Event(enable_timing=True)
-    m0.record()
-    nmv = 10
-    for _ in range(nmv):
-        V.vsie_matvec(ctx, p, Xm.data_ptr(), N, Ym.data_ptr(), N, V.VSIE_C64)
-    m1.record()
-    torch.cuda.synchronize()
-    matvecs_per_s = job_value(world, nmv * p, max_over_ranks(m0.elapsed_time(m1) / 1e3, dist, "cuda"))
-
-    # ---------------- roofline of the FFT convolution (K1), from the timed region
+    # ---------------- roofline of the FFT convolution (K1) over the timed steps
     peak, peak_src = _peaks()
     g0 = groups["fft_conv"]
-    n_groups = max(g0["launches"] // 5, 1)        # one group = 5 pass kernels
+    n_groups = max(g0["launches"] // 5, 1)        # one launch group = 5 pass kernels
     avg_ms = g0["ms"] / n_groups
     alg_per_launch = g0["alg_bytes"] / n_groups
+    rhs_per_group = p * args.steps / n_groups
     achieved = alg_per_launch / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else None
-    roofline = {"bound": "hbm", "kernel": "fft_conv (K1, 5 passes, FP32 inner operator)",
+    spec_b = 6.0 * 257 * 257 * 225 * 8
+    compulsory = (6.0 * 256 * 256 * 224 * 8) * rhs_per_group + spec_b
+    roofline = {"bound": "hbm", "kernel": "fft_conv (K1, 5 passes, FP32 operator)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_src,
-                "traffic": _traffic_per_launch(p),
-                "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms}
+                "traffic": _traffic_per_launch(rhs_per_group),
+                "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_ms,
+                "rhs_per_launch": rhs_per_group,
+                "compulsory_frac": (compulsory / (avg_ms / 1e3) / 1e9) / peak if avg_ms > 0 else None}
     total_group_ms = sum(v["ms"] for v in groups.values())
     for v in groups.values():
         v["share"] = v["ms"] / total_group_ms if total_group_ms else None
 
+    # ---------------- time to 1e-6: the 16 port right-hand sides, mixed solve
+    solve = None
+    if not args.no_solve:
+        B = torch.zeros((p, N), dtype=torch.complex128, device="cuda")
+        V.vsie_rhs_ports(ctx, list(range(p)), 1.0, B.data_ptr(), N)
+        X = torch.zeros_like(B)
+        o = V.vsie_solve_opts()
+        o.mode, o.restart, o.maxit, o.inner_tol, o.precond = 1, 50, 1, 1e-3, 0
+        V.vsie_solve(ctx, p, B.data_ptr(), N, X.data_ptr(), N, 1e-6, o)   # allocates the workspace
+        o.maxit = 4000
+        solve = _solve_stats(V, ctx, p, B, X, N, o, torch)
+        solve["restart"] = 50
+        del B, X
+    V.vsie_destroy(ctx)
+    torch.cuda.empty_cache()
+
+    head2 = None
+    if not args.no_head2mm and rank == 0:
+        head2 = head_2mm_solves(V, I, torch, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        t_mv, cores = cpu_oracle_matvec_seconds(reps=2)
-        cpu_val = 1.0 / (t_mv * ORACLE_MATVECS_PER_SOLVE)
-        cpu = {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": (f"oracle FFT body-operator matvec (96x96x112, FP64, 1 RHS) {t_mv:.2f} s, "
-                          f"scaled by {ORACLE_MATVECS_PER_SOLVE} operator applications per RHS "
-                          f"solve; surface blocks omitted")}
+        ob = OracleBody()
+        t_mv = min(ob.apply(), ob.apply())
+        cpu = {"value": 1.0 / t_mv, "unit": UNIT, "cores": ob.cores, "kind": "oracle",
+               "sample": (f"oracle FFT body operator (FP64, scipy.fft) on the same 1 mm grid, one right-hand "
+                          f"side, best of 2: {t_mv:.2f} s; surface blocks omitted (their oracle assembly does "
+                          f"not finish in bounded time; they only add time)")}
+        if solve is not None:
+            apps = (solve["fp32_matvecs"] + solve["fp64_matvecs"]) / p
+            cpu["time_to_1e-6_s_per_rhs_extrapolated"] = t_mv * apps
+            cpu["extrapolation"] = (f"x {apps:.1f} operator applications per right-hand side, the count the "
+                                    f"GPU solve of this run measured")
 
-    V.vsie_destroy(ctx)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64 inner operator, basis and Gram-Schmidt; c128 outer residual and Givens",
+            "dtype": "c64 (FP32 complex operator; the solve adds an FP64 outer residual and Givens)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": world * p, "rhs_per_gpu": p,
-                       "N_unknowns": N, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "working set larger than L2 (Krylov basis ~20 GB per solve)"},
-            "time_to_1e-6_s": ms_step / 1e3, "converged": conv_ok, "max_relres": relres,
-            "mean_inner_iters": iters, "fp32_matvecs_per_solve": mv32,
-            "matvecs_per_s": matvecs_per_s, "setup_s": setup_s,
+                       "N_unknowns": N, "m_f": mf, "m_n": mn, "n_b": nb,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (3.2 GB per 16-RHS block)"},
+            "setup_s": setup_s,
+            "time_to_1e-6": solve,
+            "head_2mm": head2,
             "roofline": roofline, "kernel_groups": groups, "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
