@@ -248,6 +248,27 @@ def _solve_stats(V, ctx, p, B, X, N, opts, torch, tol=1e-6):
             "fp64_matvecs": info.matvecs64}
 
 
+def device_rates(torch):
+    """Dense FP64 and FP32 (no TF32) GEMM rates of this GPU through torch (cuBLAS),
+    TFLOP/s, by CUDA events: the arithmetic ceilings of the FP64 operator and of
+    the FFT butterflies (SIMT FP32)."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64_gemm_tflops", torch.float64, 8192), ("fp32_simt_gemm_tflops", torch.float32, 8192)):
+            a = torch.randn((n, n), dtype=dt, device="cuda")
+            b = torch.randn((n, n), dtype=dt, device="cuda")
+            c = a @ b
+            s = _cuda_time(lambda: torch.matmul(a, b, out=c), 5, torch)
+            out[name] = 2.0 * n ** 3 * 5 / s / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
 def head_2mm_solves(V, I, torch, args):
     """The 2 mm head (96 x 96 x 112, 8 ports) with a dense far block: one mixed
     solve and one plain FP64 solve to 1e-6 (same context, same preconditioner)."""
@@ -443,6 +464,7 @@ def main():
     V.vsie_destroy(ctx)
     torch.cuda.empty_cache()
 
+    rates = device_rates(torch)
     head2 = None
     if not args.no_head2mm and rank == 0:
         head2 = head_2mm_solves(V, I, torch, args)
@@ -476,6 +498,7 @@ def main():
             "time_to_1e-6": solve,
             "head_2mm": head2,
             "roofline": roofline, "kernel_groups": groups, "gpu_launches": launches,
+            "device_rates": rates,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -16,6 +16,7 @@
 // input once and its output once.  Shared memory holds [k][line] tiles.
 #include "fft.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 
@@ -715,6 +716,9 @@ void conv_autotune(Ctx& c) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    auto& al = c.allocs;   // the scratch vectors are not kept with the context
+    al.erase(std::remove(al.begin(), al.end(), (void*)xy), al.end());
+    cudaFree(xy);
 }
 
 template <typename R>

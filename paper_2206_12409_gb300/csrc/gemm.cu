@@ -219,10 +219,34 @@ static void launch_ts(Ctx& c, bool conjA, int M, int N, int K, cx<R> alpha, cons
 }
 
 template <typename R, int BM, int BN, int TM, int TN>
+static void launch1(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+                    int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
+                    cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
+                    const uint8_t* maskC, cudaStream_t st);
+
+// Column tiles go to gridDim.y (at most 65535): wider products run in column
+// chunks (a TT factor over a 1 mm head grid has ~10^7 columns).
+template <typename R, int BM, int BN, int TM, int TN>
 static void launch(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
                    int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
                    cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
                    const uint8_t* maskC, cudaStream_t st) {
+    const int maxN = 65535 * BN;
+    for (int n0 = 0; n0 < N; n0 += maxN) {
+        const int nn = std::min(maxN, N - n0);
+        const cx<R>* Bc = opB == OP_N ? B + (size_t)n0 * ldb : B + n0;
+        launch1<R, BM, BN, TM, TN>(c, opA, opB, M, nn, K, alpha, A, lda, sA, Bc, ldb, sB, beta,
+                                   C + (size_t)n0 * ldc, ldc, sC, batch,
+                                   maskB ? maskB + (size_t)n0 * K : nullptr,
+                                   maskC ? maskC + (size_t)n0 * M : nullptr, st);
+    }
+}
+
+template <typename R, int BM, int BN, int TM, int TN>
+static void launch1(Ctx& c, GemmOp opA, GemmOp opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+                    int64_t lda, int64_t sA, const cx<R>* B, int64_t ldb, int64_t sB, cx<R> beta,
+                    cx<R>* C, int64_t ldc, int64_t sC, int batch, const uint8_t* maskB,
+                    const uint8_t* maskC, cudaStream_t st) {
     OpData<R>& d = data<R>(c);
     const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
     const int ktiles = (K + BK - 1) / BK;
