@@ -235,6 +235,12 @@ struct Scratch {
     double* bv = nullptr;
     int64_t* bi = nullptr;
     double* bs = nullptr;
+    Scratch() {
+        // split-K workspace of the set-up's GEMMs (Gram matrices of the TT factors
+        // reduce over ~10^7 columns at the 1 mm head grid)
+        c.f64.splitk_elems = (size_t)4 << 20;
+        c.f64.splitk = (double2*)dalloc(c, c.f64.splitk_elems * sizeof(double2));
+    }
     ~Scratch() {
         for (void* p : c.allocs) cudaFree(p);
     }
