@@ -101,6 +101,9 @@ typedef struct {
                               m_f >= 8192, else dense; 1 = hierarchical; -1 = dense     */
     int32_t hm_leaf;       /* H-matrix leaf cluster size, <= 256 (default 128)          */
     double hm_eta;         /* H-matrix admissibility min(diam) <= eta dist (default 1)  */
+    int32_t dense_gemm;    /* FP32 product with the preconditioner's dense far-block
+                              inverse: 0 = tensor cores (tcgen05, split TF32), 1 = SIMT  */
+    int32_t reserved;      /* zero                                                      */
 } vsie_options;
 
 /* Compressed operator parts, for vsie_create.  All arrays are host memory,

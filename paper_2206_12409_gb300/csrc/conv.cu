@@ -731,7 +731,16 @@ void conv_set_attrs() {
     VSIE_ATTR((k_ypass<R, 8, true>)); VSIE_ATTR((k_ypass<R, 16, true>)); VSIE_ATTR((k_ypass<R, 32, true>));
     VSIE_ATTR((k_zmul<R, 4>)); VSIE_ATTR((k_zmul<R, 8>)); VSIE_ATTR((k_zmul<R, 16>));
     VSIE_ATTR((k_zmul_h<R, 4>)); VSIE_ATTR((k_zmul_h<R, 8>)); VSIE_ATTR((k_zmul_h<R, 16>));
+#define VSIE_CARVE(k) VSIE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                                     (int)cudaSharedmemCarveoutMaxShared))
     if constexpr (sizeof(R) == 4) {
+        // the register kernels fit several CTAs per SM only with the largest carveout
+        VSIE_CARVE((k_zreg<7, 4>)); VSIE_CARVE((k_zreg<7, 8>)); VSIE_CARVE((k_zreg<7, 16>));
+        VSIE_CARVE((k_zreg<14, 2>)); VSIE_CARVE((k_zreg<14, 4>)); VSIE_CARVE((k_zreg<14, 8>));
+        VSIE_CARVE((k_yreg<16, 16, 16, false, true>)); VSIE_CARVE((k_yreg<16, 16, 16, true, false>));
+        VSIE_CARVE((k_yreg<32, 16, 8, false, true>)); VSIE_CARVE((k_yreg<32, 16, 8, true, false>));
+        VSIE_CARVE((k_xfwd_reg<16, 16, 8>)); VSIE_CARVE((k_xinv_reg<16, 16, 8>));
+        VSIE_CARVE((k_xfwd_reg<32, 16, 8>)); VSIE_CARVE((k_xinv_reg<32, 16, 8>));
         VSIE_ATTR((k_xfwd_reg<16, 16, 8>)); VSIE_ATTR((k_xfwd_reg<16, 16, 16>)); VSIE_ATTR((k_xfwd_reg<16, 16, 32>));
         VSIE_ATTR((k_xfwd_reg<32, 16, 8>)); VSIE_ATTR((k_xfwd_reg<32, 16, 16>)); VSIE_ATTR((k_xfwd_reg<32, 16, 32>));
         VSIE_ATTR((k_xinv_reg<16, 16, 8>)); VSIE_ATTR((k_xinv_reg<16, 16, 16>)); VSIE_ATTR((k_xinv_reg<16, 16, 32>));
@@ -746,6 +755,7 @@ void conv_set_attrs() {
         VSIE_ATTR((k_zreg<14, 2>)); VSIE_ATTR((k_zreg<14, 4>)); VSIE_ATTR((k_zreg<14, 8>));
     }
 #undef VSIE_ATTR
+#undef VSIE_CARVE
 }
 
 template void conv_autotune<float>(Ctx&);

@@ -207,7 +207,7 @@ void apply_learned_precond(Ctx& c, int p, const float2* X, int64_t ldx, float2* 
     Net& net = *reinterpret_cast<Net*>(c.net);
     ProfScope ps(c, PG_PRECOND, st);
     const cx<float> one = mk<float2>(1, 0), zero = mk<float2>(0, 0);
-    if (c.m_f > 0) gemm_panel(c, c.m_f, p, c.m_f, d.pc_Zffi, X, ldx, Y, ldy, st);
+    if (c.m_f > 0) apply_far_inverse32(c, p, X, ldx, Y, ldy, st);
     if (c.m_n > 0)
         cgemm<float>(c, OP_N, c.m_n, p, c.m_n, one, d.pc_Znni, c.m_n, 0, X + c.m_f, ldx, 0, zero,
                      Y + c.m_f, ldy, 0, 1, nullptr, nullptr, st);

@@ -14,7 +14,7 @@
 namespace vsie {
 
 static const char kMagic[8] = {'V', 'S', 'I', 'E', 'O', 'P', 'S', '1'};
-constexpr uint32_t kVersion = 2;   // 2: vsie_options with the H-matrix fields
+constexpr uint32_t kVersion = 3;   // 3: vsie_options with the H-matrix and GEMM fields
 
 struct FileCloser {
     void operator()(FILE* f) const { if (f) fclose(f); }

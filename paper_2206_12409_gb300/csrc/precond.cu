@@ -17,6 +17,8 @@
 
 #include <cusolverDn.h>
 
+#include <algorithm>
+
 namespace vsie {
 
 template <typename R>
@@ -40,6 +42,21 @@ __global__ void k_f32_widen(const float2* a, double2* b, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
         b[i] = make_double2(a[i].x, a[i].y);
+}
+
+// R[m * ldr + k] = A[m + lda * k] (32 x 32 tiles through shared memory)
+__global__ void k_transpose32(const float2* __restrict__ A, int64_t lda, int n, float2* __restrict__ R, int64_t ldr) {
+    __shared__ float2 t[32][33];
+    const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int m = m0 + threadIdx.x, k = k0 + j;
+        if (m < n && k < n) t[j][threadIdx.x] = A[(size_t)m + (size_t)lda * k];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int m = m0 + j, k = k0 + threadIdx.x;
+        if (m < n && k < n) R[(size_t)m * ldr + k] = t[threadIdx.x][j];
+    }
 }
 
 __global__ void k_unit_cols(float2* X, int64_t N, int p, int64_t row0) {
@@ -117,7 +134,31 @@ void build_block_precond(Ctx& c) {
             k_f32_widen<<<2048, 256>>>(A, c.f64.pc_Zffi, nn);
             VSIE_CUDA(cudaGetLastError());
         }
-        c.f32.pc_Zffi = to_panel(c, A, c.m_f, c.m_f);   // frees A
+        if (c.opts.dense_gemm == 0) {
+            // row-major copy for the tensor-core kernel (even row pitch for TMA)
+            const int mf = c.m_f;
+            const int64_t ld = (mf + 1) / 2 * 2;
+            float2* R = (float2*)dalloc(c, (size_t)mf * ld * sizeof(float2));
+            VSIE_CUDA(cudaMemset(R, 0, (size_t)mf * ld * sizeof(float2)));
+            dim3 tg((mf + 31) / 32, (mf + 31) / 32);
+            k_transpose32<<<tg, dim3(32, 8)>>>(A, mf, mf, R, ld);
+            VSIE_CUDA(cudaGetLastError());
+            VSIE_CUDA(cudaDeviceSynchronize());
+            auto& al = c.allocs;
+            al.erase(std::remove(al.begin(), al.end(), (void*)A), al.end());
+            cudaFree(A);
+            if (!tc_make_map(c.pc_map, R, mf, mf, ld))
+                throw Error(VSIE_ECUDA, "cannot encode the TMA tensor map of the far-block inverse");
+            if (!c.tc_err) {
+                c.tc_err = (int*)dalloc(c, sizeof(int));
+                VSIE_CUDA(cudaMemset(c.tc_err, 0, sizeof(int)));
+            }
+            c.f32.pc_Zffi = R;
+            c.pc_ld = ld;
+            c.pc_tc = true;
+        } else {
+            c.f32.pc_Zffi = to_panel(c, A, c.m_f, c.m_f);   // frees A
+        }
     }
     if (c.m_n > 0 && c.hZnn_direct.size() == (size_t)c.m_n * c.m_n) {
         // the set-up's direct near block Z_nn = -K_nn: the near-near block of the
@@ -188,6 +229,11 @@ __global__ void k_body_diag(const cx<R>* __restrict__ X, int64_t ldx, const cx<R
     }
 }
 
+void apply_far_inverse32(Ctx& c, int p, const float2* X, int64_t ldx, float2* Y, int64_t ldy, cudaStream_t st) {
+    if (c.pc_tc) tc_gemm(c, c.pc_map, c.m_f, p, c.m_f, X, ldx, Y, ldy, st);   // tensor cores
+    else gemm_panel(c, c.m_f, p, c.m_f, c.f32.pc_Zffi, X, ldx, Y, ldy, st);   // SIMT row panels
+}
+
 // Y = M X (X, Y: N x p, leading dimensions ldx, ldy; must not overlap)
 template <typename R>
 void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
@@ -200,7 +246,7 @@ void apply_block_precond(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, i
         if (!d.pc_Zffi)
             throw Error(VSIE_EUNSUPPORTED, "no FP64 far-block inverse (hierarchical Z_ff): use the mixed solve");
         if constexpr (sizeof(R) == 4)
-            gemm_panel(c, c.m_f, p, c.m_f, d.pc_Zffi, X, ldx, Y, ldy, st);   // FP32: row panels
+            apply_far_inverse32(c, p, X, ldx, Y, ldy, st);
         else
             cgemm<R>(c, OP_N, c.m_f, p, c.m_f, one, d.pc_Zffi, c.m_f, 0, X, ldx, 0, zero, Y, ldy, 0, 1,
                      nullptr, nullptr, st);

@@ -227,6 +227,10 @@ struct Ctx {
     bool owns_all = true;
     double2* dZff_in = nullptr;        // far-far block handed over on the device (FP64)
     bool pc_ready = false;             // block preconditioner built
+    bool pc_tc = false;                // FP32 Z_ff^-1 row-major, applied on the tensor cores
+    int64_t pc_ld = 0;                 // its row pitch (complex values, even)
+    alignas(64) unsigned char pc_map[128] = {0};   // its TMA tensor map (CUtensorMap)
+    int* tc_err = nullptr;             // device flag: a bounded wait of the tensor-core kernel ran out
     void* net = nullptr;               // attached learned body preconditioner (not owned)
     float* net_mat = nullptr;          // 2 x n_b: (eps_r - 1) / 50, sigma
     double* net_part = nullptr;        // reduction partials of the network's input scale
@@ -309,6 +313,14 @@ void build_block_precond(Ctx& c);
 void gemm_panel(Ctx& c, int M, int N, int K, const float2* P, const float2* B, int64_t ldb, float2* C,
                 int64_t ldc, cudaStream_t st);
 float2* to_panel(Ctx& c, float2* A, int M, int K);
+// Tensor-core product (tcgemm.cu): C = A B for row-major FP32 complex A (M x K,
+// row pitch lda even) described by the TMA tensor map `map` (tc_make_map), N
+// columns of B and C.  tc_make_map returns false if the map cannot be encoded.
+bool tc_make_map(void* map, const float2* A, int M, int K, int64_t lda);
+void tc_gemm(Ctx& c, const void* map, int M, int N, int K, const float2* B, int64_t ldb, float2* C, int64_t ldc,
+             cudaStream_t st);
+// Y = Z_ff^-1 X on the far rows with the FP32 block preconditioner (precond.cu)
+void apply_far_inverse32(Ctx& c, int p, const float2* X, int64_t ldx, float2* Y, int64_t ldy, cudaStream_t st);
 void from_panel(const float2* P, int M, int K, float2* A);
 // learned body preconditioner (nettrain.cu): Y = M X with the surface blocks of
 // the block preconditioner and the attached network on the body

@@ -54,7 +54,8 @@ class vsie_options(C.Structure):
     _fields_ = [("ext_n", C.c_int32 * 3), ("ext_offset", C.c_int32 * 3), ("stencil", C.c_int32),
                 ("near_radius", C.c_int32), ("colloc_rfac", C.c_double), ("tt_tol", C.c_double),
                 ("aca_tol", C.c_double), ("max_rhs", C.c_int32), ("precisions", C.c_int32),
-                ("far_hmatrix", C.c_int32), ("hm_leaf", C.c_int32), ("hm_eta", C.c_double)]
+                ("far_hmatrix", C.c_int32), ("hm_leaf", C.c_int32), ("hm_eta", C.c_double),
+                ("dense_gemm", C.c_int32), ("reserved", C.c_int32)]
 
 
 class vsie_parts(C.Structure):
@@ -197,7 +198,7 @@ def make_mesh(xyz, tri, ports=None):
 
 def make_options(ext_n=None, ext_offset=None, stencil=0, near_radius=0, colloc_rfac=0.0,
                  tt_tol=0.0, aca_tol=0.0, max_rhs=0, precisions=0, far_hmatrix=0, hm_leaf=0,
-                 hm_eta=0.0):
+                 hm_eta=0.0, dense_gemm=0):
     o = vsie_options()
     for i in range(3):
         o.ext_n[i] = int(ext_n[i]) if ext_n is not None else 0
@@ -206,6 +207,7 @@ def make_options(ext_n=None, ext_offset=None, stencil=0, near_radius=0, colloc_r
     o.tt_tol, o.aca_tol, o.max_rhs, o.precisions = float(tt_tol), float(aca_tol), int(max_rhs), \
         int(precisions)
     o.far_hmatrix, o.hm_leaf, o.hm_eta = int(far_hmatrix), int(hm_leaf), float(hm_eta)
+    o.dense_gemm = int(dense_gemm)
     return o
 
 
@@ -411,7 +413,7 @@ def parts_to_numpy(ctx, body_n):
     return out
 
 
-def setup_problem(prob, max_rhs=8, precisions=0, far_hmatrix=0, hm_leaf=0, hm_eta=0.0):
+def setup_problem(prob, max_rhs=8, precisions=0, far_hmatrix=0, hm_leaf=0, hm_eta=0.0, dense_gemm=0):
     """vsie_setup for an inputs.Problem (geometry marshalling only)."""
     g = prob.grid
     coil = shield = None
@@ -425,7 +427,7 @@ def setup_problem(prob, max_rhs=8, precisions=0, far_hmatrix=0, hm_leaf=0, hm_et
     opts = make_options(ext_n=prob.ext_n, ext_offset=prob.ext_offset, stencil=prob.stencil,
                         tt_tol=prob.tt_tol, aca_tol=prob.aca_tol, max_rhs=max_rhs,
                         precisions=precisions, far_hmatrix=far_hmatrix, hm_leaf=hm_leaf,
-                        hm_eta=hm_eta)
+                        hm_eta=hm_eta, dense_gemm=dense_gemm)
     return vsie_setup(make_grid(g.n, g.h, g.origin), prob.eps_r, prob.sigma, coil, shield,
                       prob.freq_hz, opts)
 

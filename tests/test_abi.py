@@ -49,5 +49,5 @@ def test_struct_layouts_match_header():
     # sizes computed from the C declarations (LP64): padding included
     assert C.sizeof(V.vsie_grid) == 4 * 3 + 4 + 8 + 24
     assert C.sizeof(V.vsie_mesh) == 48
-    assert C.sizeof(V.vsie_options) == 4 * 8 + 8 * 3 + 4 * 2 + 4 * 2 + 8
+    assert C.sizeof(V.vsie_options) == 4 * 8 + 8 * 3 + 4 * 2 + 4 * 2 + 8 + 4 * 2
     assert C.sizeof(V.vsie_solve_opts) == 4 * 3 + 4 + 8 + 4 + 4

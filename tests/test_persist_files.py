@@ -16,7 +16,7 @@ def test_load_rejects_bad_files(tmp_path):
     with pytest.raises(V.VsieError):
         V.vsie_load(bad)
     trunc = tmp_path / "trunc.vsie"
-    trunc.write_bytes(b"VSIEOPS1" + (2).to_bytes(4, "little") + b"\0" * 10)
+    trunc.write_bytes(b"VSIEOPS1" + (3).to_bytes(4, "little") + b"\0" * 10)
     with pytest.raises(V.VsieError):
         V.vsie_load(trunc)
 
@@ -27,13 +27,13 @@ def _arr(a, fmt):
 
 
 def _operator_file(port_row, port_len):
-    """A complete version-2 operator file: 2^3 vacuum body, one far RWG (a 1 x 1
+    """A complete version-3 operator file: 2^3 vacuum body, one far RWG (a 1 x 1
     Z_ff, no ACA factors, no tensor trains), no near RWG, and a port table."""
     from paper_2206_12409_gb300 import vsie as V
     g = V.make_grid((2, 2, 2), 1e-3, (0.0, 0.0, 0.0))
     o = V.make_options()
     nb = 8
-    out = b"VSIEOPS1" + struct.pack("<I", 2) + bytes(g) + struct.pack("<d", 298e6) + bytes(o)
+    out = b"VSIEOPS1" + struct.pack("<I", 3) + bytes(g) + struct.pack("<d", 298e6) + bytes(o)
     out += _arr(np.ones(nb), "<f8") + _arr(np.zeros(nb), "<f8")
     out += struct.pack("<iii", 1, 0, 3)                       # m_f, m_n, stencil
     out += _arr(np.array([1.0, 0.5]), "<f8")                  # Z_ff (1 x 1, re/im)
