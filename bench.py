@@ -393,11 +393,13 @@ def main():
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()      # scope of an ncu --profile-from-start off capture
     e0.record()
     for _ in range(args.steps):
         step()
     e1.record()
     barrier()
+    torch.cuda.profiler.stop()
     clk = clocks.stop(local)
     ms_total = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     groups = {}
