@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(R2 * NL) k_xinv_reg(ConvArgs<float> a) {
 // CTA: NL consecutive k1 columns at one k2, all three components, one RHS;
 // 32 NL threads, one (even/odd half, k1, line) item each in the middle phase.
 // Shared memory: twiddles (L3) and one exchange buffer
-// [component][even/odd][m][line], m in [0, M); the middle phase works in place
-// on the slots its item owns.
+// [component][even/odd][m][line], m in [0, M), reused by both exchanges (the
+// middle phase reads all of it before any thread overwrites it).
 template <int R2, int NL>
 __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
     using C = float2;
@@ -267,48 +267,47 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
     for (int w = threadIdx.x; w < 3 * R2 * NL; w += NT) {
         const int l = w % NL, t = (w / NL) % R2, comp = w / (NL * R2);
         const int k1g = k10 + l;
-        // the even part, then the odd part from the same (re-read, cache-resident)
-        // samples: only one 16-point line lives in registers at a time
+        C e[16], o[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int n = t + R2 * q;
+            C x = make_float2(0.f, 0.f);
+            if (n < a.n3 && k1g < a.L1) x = base[comp * cstride + (size_t)n * plane + k1g];
+            e[q] = x;
+            o[q] = cmul(x, tw[n]);
+        }
+        dftR<false>(e, int_<16>());
+        dftR<false>(o, int_<16>());
         C* de = ex + (size_t)(comp * 2) * M * NL + l;
+        C* dodd = de + (size_t)M * NL;
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            C v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int n = t + R2 * q;
-                C x = make_float2(0.f, 0.f);
-                if (n < a.n3 && k1g < a.L1) x = base[comp * cstride + (size_t)n * plane + k1g];
-                v[q] = part ? cmul(x, tw[n]) : x;
+        for (int k = 0; k < 16; ++k) {
+            C we = e[k], wo = o[k];
+            if (k > 0 && t > 0) {
+                const C tt = tw[2 * t * k];    // w_M^(t k)
+                we = cmul(we, tt);
+                wo = cmul(wo, tt);
             }
-            dftR<false>(v, int_<16>());
-            C* d = de + (size_t)part * M * NL;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                d[(t * 16 + k) * NL] = (k > 0 && t > 0) ? cmul(v[k], tw[2 * t * k]) : v[k];   // w_M^(t k)
+            de[(t * 16 + k) * NL] = we;
+            dodd[(t * 16 + k) * NL] = wo;
         }
     }
     __syncthreads();
-    // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line).  The
-    // item owns the slots m = 16 t + k1 (t < R2) of its line in all three components
-    // and works in place there, one component at a time (few live registers): after
-    // the forward DFT slot t holds frequency 2 (k1 + 16 t) + half; after the inverse
-    // DFT and its twiddle slot t holds the sample n1 = t of inverse stage B.
+    // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line)
     {
         const int w = threadIdx.x;
         const int l = w % NL, k1 = (w / NL) % 16, half = w / (16 * NL);
         const int k1g = k10 + l;
-        C* slot[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) slot[c] = ex + (size_t)(c * 2 + half) * M * NL + k1 * NL + l;
+        C v[3][R2];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            C v[R2];
+            const C* src = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
-            for (int t = 0; t < R2; ++t) v[t] = slot[c][t * 16 * NL];
-            dftR<false>(v, int_<R2>());
-#pragma unroll
-            for (int t = 0; t < R2; ++t) slot[c][t * 16 * NL] = v[t];
+            for (int t = 0; t < R2; ++t) v[c][t] = src[(t * 16 + k1) * NL];
         }
+        __syncthreads();   // every item has read its inputs; the buffer is reused below
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dftR<false>(v[c], int_<R2>());   // v[c][q]: frequency 2 (k1 + 16 q) + half
         if (k1g < a.L1) {
             const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
             const int kk2 = k2 <= a.L2 / 2 ? k2 : a.L2 - k2;
@@ -317,7 +316,7 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
             const float sg1 = k1g <= a.L1 / 2 ? 1.f : -1.f;
             const C* sp = a.spec + kk1 + (size_t)a.Lh1 * kk2;
             const size_t st3 = (size_t)a.Lh1 * a.Lh2;
-#pragma unroll 2
+#pragma unroll
             for (int q = 0; q < R2; ++q) {
                 const int k3 = 2 * (k1 + 16 * q) + half;
                 const int kk3 = k3 <= L3 / 2 ? k3 : L3 - k3;
@@ -327,23 +326,21 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
                 const C txy = cscale(so[3 * oct], sg1 * sg2);
                 const C txz = cscale(so[4 * oct], sg1 * sg3);
                 const C tyz = cscale(so[5 * oct], sg2 * sg3);
-                const C x = slot[0][q * 16 * NL], yv = slot[1][q * 16 * NL], z = slot[2][q * 16 * NL];
+                const C x = v[0][q], yv = v[1][q], z = v[2][q];
                 C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
                 cfma(ox, txy, yv); cfma(ox, txz, z);
                 cfma(oy, tyy, yv); cfma(oy, tyz, z);
                 cfma(oz, tyz, yv); cfma(oz, tzz, z);
-                slot[0][q * 16 * NL] = ox; slot[1][q * 16 * NL] = oy; slot[2][q * 16 * NL] = oz;
+                v[0][q] = ox; v[1][q] = oy; v[2][q] = oz;
             }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            C v[R2];
-#pragma unroll
-            for (int t = 0; t < R2; ++t) v[t] = slot[c][t * 16 * NL];
-            dftR<true>(v, int_<R2>());      // v[n1] = sum_q X[k1 + 16 q] w_R2^(-q n1)
+            dftR<true>(v[c], int_<R2>());      // v[c][n1] = sum_q X[k1 + 16 q] w_R2^(-q n1)
+            C* dst = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
             for (int n1 = 0; n1 < R2; ++n1)
-                slot[c][n1 * 16 * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[n1], tw[2 * n1 * k1]) : v[n1];
+                dst[(k1 * R2 + n1) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
         }
     }
     __syncthreads();
@@ -352,12 +349,12 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
         const int l = w % NL, n1 = (w / NL) % R2, comp = w / (NL * R2);
         const int k1g = k10 + l;
         C e[16], o[16];
-        const C* se = ex + (size_t)(comp * 2) * M * NL + (size_t)n1 * 16 * NL + l;
+        const C* se = ex + (size_t)(comp * 2) * M * NL + l;
         const C* so = se + (size_t)M * NL;
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
-            e[k1] = se[k1 * NL];
-            o[k1] = so[k1 * NL];
+            e[k1] = se[(k1 * R2 + n1) * NL];
+            o[k1] = so[(k1 * R2 + n1) * NL];
         }
         dftR<true>(e, int_<16>());
         dftR<true>(o, int_<16>());

@@ -582,6 +582,11 @@ void hm_build(Ctx& c, const HmPlan& P, const double2* dZ, int64_t ldz, double to
     H.xt32 = (float2*)H.xt64;   // FP32 and FP64 products never run at the same time
     H.t32 = (float2*)H.t64;
     H.ndense = (int)dense_ids.size();
+    {   // one thread per row of the largest leaf row cluster (a warp multiple)
+        int mr = 1;
+        for (size_t l = 0; l + 1 < P.rl_start.size(); ++l) mr = std::max(mr, P.rl_start[l + 1] - P.rl_start[l]);
+        H.rows_threads = std::min(256, (mr + 31) / 32 * 32);
+    }
     VSIE_CUDA(cudaDeviceSynchronize());
     H.on = true;
     if (std::getenv("VSIE_TRACE")) {
@@ -611,11 +616,11 @@ void hm_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
         k_hm_gather<R><<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 16), 256, 0, st>>>(H.m, pc, H.perm, Xc, ldx, xt);
         if (pc <= 8) {
             if (H.nlr) k_hm_vt<R, 8><<<H.nlr, 256, 0, st>>>(H.m, pc, H.lr, H.blk, H.kb, H.voff, H.toff, V, xt, t);
-            k_hm_rows<R, 8><<<H.nrl, 256, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
+            k_hm_rows<R, 8><<<H.nrl, H.rows_threads, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
                                                   H.doff, D, U, H.toff, t, xt, Yc, ldy);
         } else {
             if (H.nlr) k_hm_vt<R, 16><<<H.nlr, 256, 0, st>>>(H.m, pc, H.lr, H.blk, H.kb, H.voff, H.toff, V, xt, t);
-            k_hm_rows<R, 16><<<H.nrl, 256, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
+            k_hm_rows<R, 16><<<H.nrl, H.rows_threads, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
                                                    H.doff, D, U, H.toff, t, xt, Yc, ldy);
         }
         prof_count(c, H.nlr ? 3 : 2);

@@ -145,7 +145,7 @@ struct Prof {
 // Hierarchical far-far block (hmatrix.cu): index structures and data, device.
 struct HmDev {
     bool on = false;
-    int m = 0, nrl = 0, nblk = 0, nlr = 0, nt = 0, ndense = 0;
+    int m = 0, nrl = 0, nblk = 0, nlr = 0, nt = 0, ndense = 0, rows_threads = 256;
     int64_t nD = 0, nU = 0, nV = 0;
     int* perm = nullptr;       // cluster position -> RWG index
     int* rl = nullptr;         // leaf row clusters (nrl + 1)
