@@ -332,6 +332,31 @@ def profile_matvec(args):
     return 0
 
 
+def profile_precond(args):
+    """The block preconditioner (tensor-core far-block inverse, near-block inverse,
+    body diagonal) applied once to the 8 port columns of the 2 mm head, after
+    three warm-up applications, bracketed by cudaProfilerStart/Stop."""
+    import torch
+    from paper_2206_12409_gb300 import inputs as I
+    from paper_2206_12409_gb300 import vsie as V
+    prob = I.problem_head()
+    p = prob.nrhs
+    ctx = V.setup_problem(prob, max_rhs=p)
+    N = V.vsie_sizes(ctx)[0]
+    X = torch.randn((p, N), dtype=torch.complex64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        V.vsie_precond_apply(ctx, p, X.data_ptr(), N, Y.data_ptr(), N, 0)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    V.vsie_precond_apply(ctx, p, X.data_ptr(), N, Y.data_ptr(), N, 0)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    V.vsie_destroy(ctx)
+    print("profiled one preconditioner application, 2 mm head, p =", p)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,9 +370,13 @@ def main():
     ap.add_argument("--profile-matvec", type=int, default=0, metavar="P",
                     help="only run one bracketed FP32 body matvec with P right-hand sides (for ncu)")
     ap.add_argument("--profile-grid", default="2mm", choices=["2mm", "1mm"])
+    ap.add_argument("--profile-precond", action="store_true",
+                    help="only run one bracketed block-preconditioner application (2 mm head, for ncu)")
     args = ap.parse_args()
     if args.profile_matvec:
         return profile_matvec(args)
+    if args.profile_precond:
+        return profile_precond(args)
     if args.impl == "reference":
         return run_reference(args)
 
