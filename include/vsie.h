@@ -225,6 +225,27 @@ VSIE_API vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t
 VSIE_API vsie_status vsie_rhs_planewave(vsie_ctx* ctx, const double k_hat[3], const double e0[3], void* B,
                                         vsie_stream stream);
 
+/* Lumped loads (Sec. IV.B, V: tuning and matching elements of the coil ports):
+ * impedance z_load[2 i] + i z_load[2 i + 1] ohms in series with the edge of port
+ * ports[i] (index into [shield ports; coil ports]).  Its voltage drop enters the
+ * port row, so the operator's diagonal entry of that edge gains
+ * i omega eps0 Z_L l^2 (l the edge length); vsie_matvec and vsie_solve apply it
+ * in both precisions.  The block preconditioner is not rebuilt.  Replaces the
+ * previous loads; nloads = 0 removes them; vsie_save does not store them.  EINVAL for bad indices, a port
+ * listed twice or non-finite values.  Synchronous. */
+VSIE_API vsie_status vsie_set_loads(vsie_ctx* ctx, int32_t nloads, const int32_t* ports, const double* z_load);
+
+/* Network parameters of the listed ports (Sec. V): X (device, double2, N x nports,
+ * leading dimension ldx) holds the solutions with port j driven by 1 V
+ * (vsie_rhs_ports with V = 1) and the others shorted.  The current through port
+ * edge i is I_ij = x_i l_i, so the admittance matrix is Y = I (siemens); the
+ * impedance matrix Z = Y^-1 (ohms) and the scattering matrix
+ * S = (Z - z0)(Z + z0)^-1 for the reference impedance z0 (ohms).  Y, Z, S (host,
+ * any may be NULL): nports x nports complex, column-major, interleaved (re, im).
+ * EBREAKDOWN when Y or Z + z0 is singular.  Synchronous. */
+VSIE_API vsie_status vsie_port_network(vsie_ctx* ctx, int32_t nports, const int32_t* ports, const void* X,
+                                       int64_t ldx, double z0, double* Y, double* Z, double* S);
+
 /* Solve Z X = B for p right-hand sides to relative FP64 residual tol (Sec. III.A:
  * GMRES with restart; x0 = 0).  B, X: device double2 (C128), column-major N x p.
  * mode 0: every matvec, orthogonalisation and Givens update in FP64.

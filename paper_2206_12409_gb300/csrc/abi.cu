@@ -442,6 +442,7 @@ static void matvec_impl(Ctx& c, int p, const void* X, int64_t ldx, void* Y, int6
     surface_pre<R>(c, p, x, ldx, st);
     conv_apply<R>(c, p, x, ldx, y, ldy, st);
     surface_apply<R>(c, p, x, ldx, y, ldy, st);
+    apply_loads<R>(c, p, x, ldx, y, ldy, st);
 }
 
 template <typename R>

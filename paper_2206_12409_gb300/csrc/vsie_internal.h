@@ -194,6 +194,10 @@ struct Ctx {
     int tt_rank[3][3] = {{0}};
     std::vector<double> port_len;      // per port: edge length (far ports first)
     std::vector<int64_t> port_row;     // per port: unknown index
+    int nloads = 0;                    // lumped loads on port edges (ports.cu)
+    int64_t* load_rows = nullptr;      // device: loaded unknowns
+    double2* load_d64 = nullptr;       // device: i omega eps0 Z_L l^2 per load
+    float2* load_d32 = nullptr;
     // device index structures (precision independent)
     uint8_t* mask = nullptr;           // n_b material flags
     int32_t* line_ptr = nullptr;       // per ext line (i2,i3): CSR of active voxels
@@ -307,6 +311,9 @@ void conv_set_attrs();
 template <typename R>
 void conv_autotune(Ctx& c);
 void build_block_precond(Ctx& c);
+// lumped loads (ports.cu): Y += diag(loads) X on the loaded rows
+template <typename R>
+void apply_loads(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy, cudaStream_t st);
 // FP32 row-panel storage of the dense far blocks (gemm.cu): C = P B for
 // N right-hand sides; to_panel converts a column-major M x K matrix (lda = M,
 // freed) into a new panel allocation; from_panel writes it back column-major.

@@ -26,6 +26,7 @@ __all__ = [
     "loop_strip", "closed_cylinder", "open_cylinder", "loop_array_on_cylinder",
     "merge_meshes", "random_vectors", "problem_sphere_loop_shield",
     "problem_head", "problem_volume_only", "problem_coil_array_mid", "problem_head_1mm",
+    "problem_two_loops",
 ]
 
 
@@ -407,3 +408,15 @@ def problem_head_1mm(freq_hz=298e6, seed=0, nrhs=16):
     return problem_head(n_body=(192, 192, 224), h=1e-3, freq_hz=freq_hz, ext_n=(256, 256, 224),
                         n_loops=16, loop_seg=256, shield_theta=200, shield_z=100, tt_tol=1e-5,
                         aca_tol=1e-5, seed=seed, nrhs=nrhs)
+
+
+def problem_two_loops(freq_hz=298e6):
+    """Port-network case: a 6^3 sphere at 10 mm (r = 25 mm, eps_r 50, sigma 0.6),
+    two strip loops on a 40 mm cylinder (32 segments each, 2 ports) and a small
+    closed cylinder shield, on a 12 x 12 x 6 extended grid; TT and ACA at 1e-6."""
+    g, er, sg = sphere_phantom((6, 6, 6), 10e-3, 25e-3, 50.0, 0.6)
+    coil = loop_array_on_cylinder(n_loops=2, radius=0.04, height=0.03, width=3e-3, gap=10e-3,
+                                  corner=6e-3, n_seg=32)
+    shield = closed_cylinder(0.1, 0.2, n_theta=8, n_z=2, n_rings=2)
+    return Problem("two loops", g, er, sg, freq_hz, coil, shield, (12, 12, 6), (3, 3, 0), 3,
+                   1e-6, 1e-6, 2)

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
                 7: "VSIE_EUNSUPPORTED"}
 
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
-           "vsie_matvec", "vsie_rhs_ports", "vsie_rhs_planewave", "vsie_solve", "vsie_save", "vsie_load",
+           "vsie_matvec", "vsie_rhs_ports", "vsie_rhs_planewave", "vsie_set_loads", "vsie_port_network",
+           "vsie_solve", "vsie_save", "vsie_load",
            "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_volume_matvec_static",
            "vsie_net_create", "vsie_net_num_params", "vsie_net_set_params", "vsie_net_get_params",
            "vsie_net_forward", "vsie_net_backward", "vsie_net_step", "vsie_net_train",
@@ -110,6 +111,11 @@ def load_library(path: str | None = None):
     lib.vsie_rhs_ports.argtypes = [P, C.c_int32, C.POINTER(C.c_int32), C.c_double, P, C.c_int64, P]
     lib.vsie_rhs_planewave.restype = C.c_int
     lib.vsie_rhs_planewave.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double), P, P]
+    lib.vsie_set_loads.restype = C.c_int
+    lib.vsie_set_loads.argtypes = [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    lib.vsie_port_network.restype = C.c_int
+    lib.vsie_port_network.argtypes = [P, C.c_int32, C.POINTER(C.c_int32), P, C.c_int64, C.c_double,
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.vsie_solve.restype = C.c_int
     lib.vsie_solve.argtypes = [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_double,
                                C.POINTER(vsie_solve_opts), C.POINTER(vsie_solve_info), P]
@@ -311,6 +317,24 @@ def vsie_rhs_planewave(ctx, k_hat, e0, B, stream=0):
     kh = (C.c_double * 3)(*[float(v) for v in k_hat])
     ev = (C.c_double * 3)(*[float(v) for v in e0])
     _check(lib.vsie_rhs_planewave(ctx, kh, ev, C.c_void_p(int(B)), C.c_void_p(int(stream))), ctx)
+
+
+def vsie_set_loads(ctx, ports, z_load):
+    """Lumped loads: z_load complex ohms in series with the listed port edges."""
+    z = np.asarray(z_load, np.complex128).ravel()
+    pr = (C.c_int32 * max(len(ports), 1))(*[int(x) for x in ports])
+    zz = np.ascontiguousarray(np.stack([z.real, z.imag], -1).ravel(), np.float64)
+    _check(load_library().vsie_set_loads(ctx, len(ports), pr, _dptr(zz) if len(ports) else None), ctx)
+
+
+def vsie_port_network(ctx, ports, X, ldx, z0=50.0):
+    """Y, Z, S (numpy complex, nports x nports) from the solutions X (device)."""
+    n = len(ports)
+    pr = (C.c_int32 * n)(*[int(x) for x in ports])
+    out = [np.zeros(2 * n * n, np.float64) for _ in range(3)]
+    _check(load_library().vsie_port_network(ctx, n, pr, C.c_void_p(int(X)), int(ldx), float(z0),
+                                             *[_dptr(o) for o in out]), ctx)
+    return tuple(o.view(np.complex128).reshape(n, n, order="F") for o in out)
 
 
 def vsie_solve(ctx, p, B, ldb, X, ldx, tol, opts=None, stream=0, check=True):
