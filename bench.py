@@ -509,10 +509,13 @@ def main():
                           f"side, best of 2: {t_mv:.2f} s; surface blocks omitted (their oracle assembly does "
                           f"not finish in bounded time; they only add time)")}
         if solve is not None:
-            apps = (solve["fp32_matvecs"] + solve["fp64_matvecs"]) / p
+            # one operator application per inner iteration of a right-hand side, plus
+            # the FP64 refinement residuals (each block matvec of the solve applies the
+            # operator to all p columns at once)
+            apps = solve["mean_inner_iters"] + solve["fp64_matvecs"]
             cpu["time_to_1e-6_s_per_rhs_extrapolated"] = t_mv * apps
-            cpu["extrapolation"] = (f"x {apps:.1f} operator applications per right-hand side, the count the "
-                                    f"GPU solve of this run measured")
+            cpu["extrapolation"] = (f"x {apps:.1f} operator applications per right-hand side (mean inner "
+                                    f"iterations + FP64 residuals of the GPU solve of this run)")
 
     if rank == 0:
         line = {

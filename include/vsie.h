@@ -154,8 +154,8 @@ typedef struct {
     int32_t iters[64];      /* inner iterations per RHS (first 64 RHS)                   */
     double relres[64];      /* final true relative residual ||b - Z x|| / ||b|| (FP64)   */
     int32_t outer;          /* refinement steps taken (mode 1)                           */
-    int32_t matvecs64;      /* FP64 operator applications                                 */
-    int32_t matvecs32;      /* FP32 operator applications                                 */
+    int32_t matvecs64;      /* FP64 block operator applications (each over the p columns) */
+    int32_t matvecs32;      /* FP32 block operator applications (each over the p columns) */
     double seconds;         /* wall time of the solve                                     */
 } vsie_solve_info;
 
@@ -224,6 +224,17 @@ VSIE_API vsie_status vsie_rhs_ports(vsie_ctx* ctx, int32_t nports, const int32_t
  * Asynchronous on `stream`. */
 VSIE_API vsie_status vsie_rhs_planewave(vsie_ctx* ctx, const double k_hat[3], const double e0[3], void* B,
                                         vsie_stream stream);
+
+/* One right-hand side with several ports driven at once (Sec. V: a coil array
+ * driven in a chosen mode, e.g. the circularly polarised mode of an n-loop array,
+ * v_k = exp(-i 2 pi k / n) for loop k): port ports[i] (index into [shield ports;
+ * coil ports]) carries the delta-gap voltage v[2 i] + i v[2 i + 1] volts, so its
+ * row is i omega eps0 v_i l; every other entry of B (device, double2, N values) is
+ * zero.  EINVAL for bad indices, a port listed twice or non-finite voltages.
+ * Asynchronous on `stream` after a synchronous upload of the nports values; it
+ * returns once the entries are written. */
+VSIE_API vsie_status vsie_rhs_drive(vsie_ctx* ctx, int32_t nports, const int32_t* ports, const double* v, void* B,
+                                    vsie_stream stream);
 
 /* Lumped loads (Sec. IV.B, V: tuning and matching elements of the coil ports):
  * impedance z_load[2 i] + i z_load[2 i + 1] ohms in series with the edge of port

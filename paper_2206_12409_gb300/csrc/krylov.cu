@@ -587,14 +587,14 @@ vsie_status solve_impl(Ctx& c, int p, const double2* B, int64_t ldb, double2* X,
             std::vector<double> rn2;
             K64.norms(rn2);
             if (c.tc_err) {   // a bounded wait of the tensor-core preconditioner kernel ran out
-        int e = 0;
-        VSIE_CUDA(cudaMemcpy(&e, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) {
-            VSIE_CUDA(cudaMemset(c.tc_err, 0, sizeof(int)));
-            throw Error(VSIE_ETIMEOUT, "tensor-core far-block kernel: a bounded wait ran out");
-        }
-    }
-    bool conv = true;
+                int e = 0;
+                VSIE_CUDA(cudaMemcpy(&e, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+                if (e) {
+                    VSIE_CUDA(cudaMemset(c.tc_err, 0, sizeof(int)));
+                    throw Error(VSIE_ETIMEOUT, "tensor-core far-block kernel: a bounded wait ran out");
+                }
+            }
+            bool conv = true;
             for (int q = 0; q < p; ++q) {
                 relres[q] = bn[q] > 0 ? std::sqrt(rn2[q]) / bn[q] : 0.0;
                 if (!std::isfinite(relres[q])) throw Error(VSIE_EBREAKDOWN, "non-finite residual");

@@ -42,6 +42,31 @@ void apply_loads(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t l
 template void apply_loads<float>(Ctx&, int, const float2*, int64_t, float2*, int64_t, cudaStream_t);
 template void apply_loads<double>(Ctx&, int, const double2*, int64_t, double2*, int64_t, cudaStream_t);
 
+// I_ij = x_j[row_i] l_i (current through port edge i for the drive of port j)
+__global__ void k_port_currents(int n, const int64_t* __restrict__ rows, const double* __restrict__ len,
+                                const double2* __restrict__ X, int64_t ldx, double2* __restrict__ I) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int i = e % n, j = e / n;
+    const double2 x = X[(size_t)j * ldx + rows[i]];
+    I[e] = make_double2(x.x * len[i], x.y * len[i]);
+}
+
+// one column: port edge m_i driven by the complex voltage v_i
+__global__ void k_drive_entries(int n, const int64_t* __restrict__ rows, const double2* __restrict__ b,
+                                double2* __restrict__ B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) B[rows[i]] = b[i];
+}
+
+template <typename T> struct TmpBuf {
+    T* p = nullptr;
+    explicit TmpBuf(size_t n) { VSIE_CUDA(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T))); }
+    ~TmpBuf() { if (p) cudaFree(p); }
+    TmpBuf(const TmpBuf&) = delete;
+    TmpBuf& operator=(const TmpBuf&) = delete;
+};
+
 // Gauss-Jordan inverse with partial pivoting of a small complex matrix
 // (column-major); false if singular.
 static bool small_inverse(int n, std::vector<std::complex<double>>& A) {
@@ -149,17 +174,24 @@ extern "C" vsie_status vsie_port_network(vsie_ctx* ctx, int32_t nports, const in
         if (ldx < c->N) throw Error(VSIE_EINVAL, "leading dimension < N");
         if (!(z0 > 0) || !std::isfinite(z0)) throw Error(VSIE_EINVAL, "reference impedance must be > 0");
         const int n = nports;
-        std::vector<std::complex<double>> I((size_t)n * n);
+        std::vector<int64_t> hrow(n);
+        std::vector<double> hlen(n);
         for (int i = 0; i < n; ++i) {
             const int q = ports[i];
             if (q < 0 || q >= (int)c->port_row.size()) throw Error(VSIE_EINVAL, "port index out of range");
-            for (int j = 0; j < n; ++j) {
-                double2 v;
-                VSIE_CUDA(cudaMemcpy(&v, (const double2*)X + (size_t)j * ldx + c->port_row[q], sizeof(double2),
-                                     cudaMemcpyDeviceToHost));
-                I[i + (size_t)n * j] = std::complex<double>(v.x, v.y) * c->port_len[q];   // 1 V drive
-            }
+            hrow[i] = c->port_row[q];
+            hlen[i] = c->port_len[q];
         }
+        // gather I_ij = x_j[row_i] l_i on the device, one copy back
+        TmpBuf<int64_t> drow(n);
+        TmpBuf<double> dlen(n);
+        TmpBuf<double2> dI((size_t)n * n);
+        VSIE_CUDA(cudaMemcpy(drow.p, hrow.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+        VSIE_CUDA(cudaMemcpy(dlen.p, hlen.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        k_port_currents<<<(n * n + 127) / 128, 128>>>(n, drow.p, dlen.p, (const double2*)X, ldx, dI.p);
+        VSIE_CUDA(cudaGetLastError());
+        std::vector<std::complex<double>> I((size_t)n * n);
+        VSIE_CUDA(cudaMemcpy(I.data(), dI.p, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToHost));
         put(Y, I);
         std::vector<std::complex<double>> Zm = I;
         if (!small_inverse(n, Zm)) throw Error(VSIE_EBREAKDOWN, "singular admittance matrix");
@@ -177,6 +209,41 @@ extern "C" vsie_status vsie_port_network(vsie_ctx* ctx, int32_t nports, const in
                     for (int k = 0; k < n; ++k) Sm[i + (size_t)n * j] += P[i + (size_t)n * k] * Q[k + (size_t)n * j];
             put(S, Sm);
         }
+    } catch (const Error& e) {
+        c->err = e.msg;
+        return e.st;
+    }
+    return VSIE_OK;
+}
+
+extern "C" vsie_status vsie_rhs_drive(vsie_ctx* ctx, int32_t nports, const int32_t* ports, const double* v,
+                                      void* B, vsie_stream stream) {
+    if (!ctx) { set_global_err("null context"); return VSIE_EINVAL; }
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    try {
+        if (!B || nports < 1 || !ports || !v) throw Error(VSIE_EINVAL, "need B, ports and voltages");
+        std::vector<int64_t> hrow(nports);
+        std::vector<double2> hb(nports);
+        for (int i = 0; i < nports; ++i) {
+            const int q = ports[i];
+            if (q < 0 || q >= (int)c->port_row.size()) throw Error(VSIE_EINVAL, "port index out of range");
+            for (int k = 0; k < i; ++k)
+                if (ports[k] == q) throw Error(VSIE_EINVAL, "a port is listed twice");
+            if (!std::isfinite(v[2 * i]) || !std::isfinite(v[2 * i + 1])) throw Error(VSIE_EINVAL, "non-finite voltage");
+            // i omega eps0 V l: i (a + i b) = -b + i a
+            const double s = c->omega * kEps0 * c->port_len[q];
+            hrow[i] = c->port_row[q];
+            hb[i] = make_double2(-s * v[2 * i + 1], s * v[2 * i]);
+        }
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+        TmpBuf<int64_t> drow(nports);
+        TmpBuf<double2> db(nports);
+        VSIE_CUDA(cudaMemcpy(drow.p, hrow.data(), nports * sizeof(int64_t), cudaMemcpyHostToDevice));
+        VSIE_CUDA(cudaMemcpy(db.p, hb.data(), nports * sizeof(double2), cudaMemcpyHostToDevice));
+        VSIE_CUDA(cudaMemsetAsync(B, 0, c->N * sizeof(double2), st));
+        k_drive_entries<<<(nports + 127) / 128, 128, 0, st>>>(nports, drow.p, db.p, (double2*)B);
+        VSIE_CUDA(cudaGetLastError());
+        VSIE_CUDA(cudaStreamSynchronize(st));   // the staging buffers are freed on return
     } catch (const Error& e) {
         c->err = e.msg;
         return e.st;

@@ -153,6 +153,13 @@ void build_block_precond(Ctx& c) {
                 c.tc_err = (int*)dalloc(c, sizeof(int));
                 VSIE_CUDA(cudaMemset(c.tc_err, 0, sizeof(int)));
             }
+            // B' workspace: 2048 floats per 16 complex k
+            c.pc_bprep_elems = (size_t)((2 * (size_t)mf + 31) / 32) * 2048;
+            c.pc_bprep = (float*)dalloc(c, c.pc_bprep_elems * sizeof(float));
+            int dev = 0, nsm = 0;
+            VSIE_CUDA(cudaGetDevice(&dev));
+            VSIE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            if (nsm > 0) c.num_sms = nsm;
             c.f32.pc_Zffi = R;
             c.pc_ld = ld;
             c.pc_tc = true;

@@ -1,10 +1,9 @@
 // Dense FP32 complex product C (M x N, N <= 16) = A (M x K) B (K x N) on the
 // 5th-generation tensor cores: tcgen05.mma (kind::tf32, M = 128, N = 32, K = 8)
-// with the accumulator in tensor memory, A streamed by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) through a 4-stage mbarrier pipeline.
-// This is the shape of the block preconditioner's far-block inverse (M = K =
-// m_f, N = p right-hand sides), which the SIMT kernel of gemm.cu computes at
-// FP32-issue rate rather than at the rate its matrix streams from HBM.
+// with the accumulator in tensor memory.  This is the shape of the block
+// preconditioner's far-block inverse (M = K = m_f, N = p right-hand sides): a
+// matrix streamed once from HBM against a thin operand, so the kernel is built
+// to keep HBM busy.
 //
 // Complex to real: row m of A, read as 2K floats (re, im interleaved), times the
 // 2K x 32 real matrix B' with
@@ -13,8 +12,25 @@
 // gives Re C in columns n and Im C in columns 16 + n.
 // Split TF32 (FP32-level accuracy): x = hi + lo with hi = tf32(x) rounded to
 // nearest and lo = x - hi; C ~= A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped
-// A_lo B_lo term is ~2^-22 relative).  The split of the A tile is done in shared
-// memory by the CTA's threads after each TMA load.
+// A_lo B_lo term is ~2^-22 relative).
+//
+// Warp roles (192 threads, one CTA per SM, 5-stage shared-memory ring of 40 KB
+// stages; a variant with a 7-stage ring of A tiles and a separate 2-slot ring of
+// A_lo tiles measured 15 % slower, the split then waiting on the MMAs):
+//   warp 0    one lane issues, per 32-float K chunk, the TMA load of the A tile
+//             (128 rows x 128 B, 128-byte swizzle) and a bulk copy of the
+//             prepared B' chunk (hi and lo, already swizzled) onto full[s];
+//   warps 2-5 split the A tile in place into hi and lo (element-wise, so the
+//             swizzle does not matter) and arrive on conv[s]; at the end they
+//             read the accumulator out of tensor memory (warp w reads lanes
+//             32 (w mod 4) .. +31) and store C;
+//   warp 1    one lane issues the 3 x 4 MMAs of a chunk and commits them to
+//             empty[s], which frees the stage for the next load.
+// B' is written once per call by k_tc_prepB (K/16 chunks of 8 KB).  The K range
+// is split over gridDim.y; partial sums go to a workspace and k_tc_reduce adds
+// them in a fixed order.  Every mbarrier wait is bounded: a wait that runs out
+// sets the error flag, the other roles then run out too, the producer waits
+// (bounded) for its copies in flight and the tensor memory is freed.
 // A must be stored row-major (K-major): row m at A + m lda, lda complex values,
 // lda even (16-byte rows for TMA).
 #include "vsie_internal.h"
@@ -27,18 +43,18 @@ namespace {
 constexpr int TC_BM = 128;                      // rows per CTA: one MMA M
 constexpr int TC_BK = 32;                       // floats of the real row view per stage (128 B)
 constexpr int TC_NP = 32;                       // real product columns (16 re + 16 im)
-constexpr int TC_ST = 4;                        // pipeline stages
+constexpr int TC_ST = 5;                        // pipeline stages
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;   // 16 KB
 constexpr int TC_B_BYTES = TC_NP * TC_BK * 4;   // 4 KB
-constexpr int TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
-constexpr int TC_THREADS = 128;
-constexpr uint32_t kSpinLimit = 1u << 24;       // bounded mbarrier waits
+constexpr int TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;   // A hi, A lo, B' hi, B' lo: 40 KB
+constexpr int TC_THREADS = 192;
+constexpr uint32_t kSpinLimit = 1u << 24;       // bounded mbarrier waits: polls
+constexpr uint64_t kWaitNs = 2000000000ull;     // and wall time (2 s)
 }  // namespace
 
 struct TcArgs {
     int M, N, K;
-    const float2* B;
-    int64_t ldb;
+    const float* Bp;   // prepared B' chunks [kc][hi 1024 | lo 1024] floats
     float2* C;
     int64_t ldc;
     float2* ws;        // split-K partials [split][n][m]
@@ -63,9 +79,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: gives up after kWaitNs of wall time (checked every 256 polls) or
+// kSpinLimit polls, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
         if (mbar_try_wait(b, parity)) return true;
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -73,6 +99,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -114,11 +148,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// B' of chunk kc (16 complex k): 32 rows (n') of 32 floats, K-major with the
+// 128-byte swizzle (16-byte unit u of row r stored at unit u ^ (r mod 8)); hi at
+// [kc][0, 1024), lo at [kc][1024, 2048).
+__global__ void k_tc_prepB(int K, int N, const float2* __restrict__ B, int64_t ldb, int nchunks, float* __restrict__ Bp) {
+    const size_t tot = (size_t)nchunks * 1024;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int kc = (int)(e >> 10), r = (int)(e & 1023);
+        const int np = r >> 5, f = r & 31;
+        const int kk = kc * (TC_BK / 2) + (f >> 1), n = np & 15;
+        float v = 0.f;
+        if (kk < K && n < N) {
+            const float2 b = B[(size_t)kk + (size_t)n * ldb];
+            v = np < 16 ? ((f & 1) ? -b.y : b.x) : ((f & 1) ? b.x : b.y);
+        }
+        const float hi = tf32_rna(v);
+        const int off = np * 32 + ((((f >> 2) ^ (np & 7))) << 2) + (f & 3);
+        Bp[(size_t)kc * 2048 + off] = hi;
+        Bp[(size_t)kc * 2048 + 1024 + off] = v - hi;
+    }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tcgemm(const __grid_constant__ CUtensorMap tmapA, TcArgs g) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[TC_ST], empty[TC_ST];
+    __shared__ uint64_t full[TC_ST], conv[TC_ST], empty[TC_ST], done;
     __shared__ uint32_t tmem_base;
+    __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM;
     const int nk_total = (2 * g.K + TC_BK - 1) / TC_BK;
@@ -127,11 +183,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tcgemm(const __grid_constant_
     if (tid == 0) {
         for (int s = 0; s < TC_ST; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 4);
             mbar_init(&empty[s], 1);
         }
+        mbar_init(&done, 1);
+        fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -140,106 +199,94 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tcgemm(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    // D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12), both K-major, N / 8 (bits 17-22), M / 16 (bits 24-28)
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_NP >> 3) << 17) |
-                           ((uint32_t)(TC_BM >> 4) << 24);
-    int issued = 0;   // TMA loads issued (thread 0)
-    if (tid == 0) {
-        for (; issued < min(TC_ST - 1, nk); ++issued) {
-            mbar_expect_tx(&full[issued], TC_A_BYTES);
-            tma_load_2d(sm + issued * TC_STAGE, &tmapA, (kc0 + issued) * TC_BK, m0, &full[issued]);
-        }
-    }
-    bool bad = false;
-    int committed = 0;   // MMA groups committed (thread 0)
-    for (int i = 0; i < nk; ++i) {
-        const int s = i % TC_ST;
-        unsigned char* st = sm + s * TC_STAGE;
-        float* Ahi = reinterpret_cast<float*>(st);
-        float* Alo = reinterpret_cast<float*>(st + TC_A_BYTES);
-        float* Bhi = reinterpret_cast<float*>(st + 2 * TC_A_BYTES);
-        float* Blo = reinterpret_cast<float*>(st + 2 * TC_A_BYTES + TC_B_BYTES);
-        const int to = mbar_wait(&full[s], (i / TC_ST) & 1) ? 0 : 1;
-        if (__syncthreads_or(to)) { bad = true; break; }
-        // B' for complex k in [16 kc, 16 kc + 16), written in the swizzled K-major layout
-        const int kc = kc0 + i;
-        for (int e = tid; e < TC_NP * TC_BK; e += TC_THREADS) {
-            const int np = e >> 5, f = e & 31;
-            const int kk = kc * (TC_BK / 2) + (f >> 1), n = np & 15;
-            float v = 0.f;
-            if (kk < g.K && n < g.N) {
-                const float2 b = g.B[(size_t)kk + (size_t)n * g.ldb];
-                v = np < 16 ? ((f & 1) ? -b.y : b.x) : ((f & 1) ? b.x : b.y);
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            bool bad = false;
+            int issued = 0;
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % TC_ST;
+                if (i >= TC_ST && !mbar_wait(&empty[s], ((i / TC_ST) - 1) & 1)) { bad = true; break; }
+                unsigned char* st = sm + s * TC_STAGE;
+                mbar_expect_tx(&full[s], TC_A_BYTES + 2 * TC_B_BYTES);
+                tma_load_2d(st, &tmapA, (kc0 + i) * TC_BK, m0, &full[s]);
+                bulk_load(st + 2 * TC_A_BYTES, g.Bp + (size_t)(kc0 + i) * 2048, 2 * TC_B_BYTES, &full[s]);
+                issued = i + 1;
             }
-            const float hi = tf32_rna(v);
-            const int off = np * 32 + ((((f >> 2) ^ (np & 7))) << 2) + (f & 3);
-            Bhi[off] = hi;
-            Blo[off] = v - hi;
+            // every copy still in flight lands before the CTA may exit (the
+            // latest phase of each stage is the only one that can be pending)
+            for (int q = max(0, issued - TC_ST); q < issued; ++q)
+                if (!mbar_wait(&full[q % TC_ST], (q / TC_ST) & 1)) bad = true;
+            if (bad) atomicExch(&fail, 1);
         }
-        // the A tile split in place (element-wise, so the swizzle does not matter)
-        for (int e = tid; e < TC_BM * TC_BK; e += TC_THREADS) {
-            const float a = Ahi[e];
-            const float hi = tf32_rna(a);
-            Ahi[e] = hi;
-            Alo[e] = a - hi;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            // D = F32 (bits 4-5), A = B = TF32 (bits 7-9, 10-12), both K-major, N / 8 (bits 17-22), M / 16 (bits 24-28)
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_NP >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            bool bad = false;
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % TC_ST;
+                if (!mbar_wait(&conv[s], (i / TC_ST) & 1)) { bad = true; break; }
+                tc_fence_after();
+                const uint32_t ah = smem_u32(sm + s * TC_STAGE), al = ah + TC_A_BYTES;
+                const uint32_t bh = ah + 2 * TC_A_BYTES, bl = bh + TC_B_BYTES;
 #pragma unroll
-            for (int j = 0; j < TC_BK / 8; ++j) {   // K = 8 TF32 (32 bytes) per MMA
-                const uint32_t o = 32u * j;
-                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (i > 0 || j > 0) ? 1u : 0u);
-                mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
-                mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
-            }
-            mma_commit(&empty[s]);
-            committed = i + 1;
-            // next load: chunk i + ST - 1 into the stage of chunk i - 1, once its MMAs are done
-            const int nx = i + TC_ST - 1;
-            if (nx < nk) {
-                const int sn = nx % TC_ST;
-                if (i >= 1 && !mbar_wait(&empty[sn], ((i - 1) / TC_ST) & 1)) {
-                    bad = true;
-                } else {
-                    mbar_expect_tx(&full[sn], TC_A_BYTES);
-                    tma_load_2d(sm + sn * TC_STAGE, &tmapA, (kc0 + nx) * TC_BK, m0, &full[sn]);
-                    issued = nx + 1;
+                for (int j = 0; j < TC_BK / 8; ++j) {   // K = 8 TF32 (32 bytes) per MMA
+                    const uint32_t o = 32u * j;
+                    mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (i > 0 || j > 0) ? 1u : 0u);
+                    mma_tf32(tmem, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
+                    mma_tf32(tmem, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
                 }
+                mma_commit(&empty[s]);
             }
+            mma_commit(&done);   // arrives once every MMA issued above has completed
+            if (bad) atomicExch(&fail, 1);
         }
-        if (__syncthreads_or(bad ? 1 : 0)) { bad = true; break; }
-    }
-    if (tid == 0) {
-        // wait for the last MMA group and for any load still in flight (bounded)
-        if (committed > 0 && !mbar_wait(&empty[(committed - 1) % TC_ST], ((committed - 1) / TC_ST) & 1)) bad = true;
-        for (int q = committed; q < issued; ++q)
-            if (!mbar_wait(&full[q % TC_ST], (q / TC_ST) & 1)) bad = true;
-        if (bad) atomicExch(g.err, 1);
-    }
-    const int any_bad = __syncthreads_or(bad ? 1 : 0);
-    tc_fence_after();
-    if (!any_bad) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
-        const int m = m0 + warp * 32 + lane;
-        if (m < g.M) {
-            if (g.splits == 1) {
-                for (int n = 0; n < g.N; ++n)
-                    g.C[(size_t)m + (size_t)n * g.ldc] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[16 + n]));
-            } else {
-                float2* w = g.ws + (size_t)blockIdx.y * g.M * g.N;
-                for (int n = 0; n < g.N; ++n)
-                    w[(size_t)m + (size_t)n * g.M] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[16 + n]));
+        __syncwarp();
+    } else {
+        // warps 2-5: split the A tile of each stage into hi (in place) and lo
+        const int ct = tid - 64;
+        bool bad = false;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_ST;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / TC_ST) & 1))) { bad = true; break; }
+            float4* Ahi = reinterpret_cast<float4*>(sm + s * TC_STAGE);
+            float4* Alo = reinterpret_cast<float4*>(sm + s * TC_STAGE + TC_A_BYTES);
+#pragma unroll
+            for (int j = 0; j < TC_A_BYTES / 16 / 128; ++j) {
+                const float4 a = Ahi[ct + 128 * j];
+                const float4 h = make_float4(tf32_rna(a.x), tf32_rna(a.y), tf32_rna(a.z), tf32_rna(a.w));
+                Ahi[ct + 128 * j] = h;
+                Alo[ct + 128 * j] = make_float4(a.x - h.x, a.y - h.y, a.z - h.z, a.w - h.w);
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
+        }
+        if (!__all_sync(0xffffffffu, mbar_wait(&done, 0))) bad = true;
+        if (bad && lane == 0) atomicExch(&fail, 1);
+    }
+    __syncthreads();
+    const bool any_bad = fail != 0;
+    if (any_bad && tid == 0) atomicExch(g.err, 1);
+    tc_fence_after();
+    if (!any_bad && warp >= 2) {
+        const int q = warp & 3;   // tensor-memory lanes 32 q .. 32 q + 31
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16), r);
+        const int m = m0 + q * 32 + lane;
+        if (m < g.M) {
+            float2* out = g.splits == 1 ? g.C : g.ws + (size_t)blockIdx.y * g.M * g.N;
+            const int64_t ld = g.splits == 1 ? g.ldc : g.M;
+#pragma unroll
+            for (int n = 0; n < 16; ++n)
+                if (n < g.N) out[(size_t)m + (size_t)n * ld] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[16 + n]));
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 __global__ void k_tc_reduce(int M, int N, int splits, const float2* __restrict__ ws, float2* __restrict__ C,
@@ -289,17 +336,28 @@ void tc_gemm(Ctx& c, const void* map, int M, int N, int K, const float2* B, int6
     OpData<float>& d = data<float>(c);
     const int mt = (M + TC_BM - 1) / TC_BM;
     const int nk = (2 * K + TC_BK - 1) / TC_BK;
+    if ((size_t)nk * 2048 > c.pc_bprep_elems) throw Error(VSIE_EINVAL, "tensor-core B workspace too small");
     for (int n0 = 0; n0 < N; n0 += 16) {
         const int nn = std::min(16, N - n0);
-        int splits = std::max(1, std::min((2 * 152 + mt - 1) / mt, nk / 16));
-        while (splits > 1 && (size_t)splits * M * nn > d.splitk_elems) --splits;
-        const int kper = (nk + splits - 1) / splits;
-        splits = (nk + kper - 1) / kper;
-        TcArgs g{M, nn, K, B + (size_t)n0 * ldb, ldb, C + (size_t)n0 * ldc, ldc, d.splitk, splits, kper, c.tc_err};
+        // split K so that waves x chunks per CTA (the time, one CTA per SM) is smallest
+        int best = 1;
+        double best_cost = 1e300;
+        for (int sp = 1; sp <= 16 && sp <= std::max(1, nk / 8); ++sp) {
+            if (sp > 1 && (size_t)sp * M * nn > d.splitk_elems) break;
+            const int kper = (nk + sp - 1) / sp;
+            const int spr = (nk + kper - 1) / kper;
+            const double cost = (double)((mt * spr + c.num_sms - 1) / c.num_sms) * kper;
+            if (cost < best_cost * 0.999) { best_cost = cost; best = sp; }
+        }
+        const int kper = (nk + best - 1) / best;
+        const int splits = (nk + kper - 1) / kper;
+        k_tc_prepB<<<(int)std::min<size_t>(((size_t)nk * 1024 + 255) / 256, 8192), 256, 0, st>>>(
+            K, nn, B + (size_t)n0 * ldb, ldb, nk, c.pc_bprep);
+        TcArgs g{M, nn, K, c.pc_bprep, C + (size_t)n0 * ldc, ldc, d.splitk, splits, kper, c.tc_err};
         CUtensorMap tm;
         memcpy(&tm, map, sizeof(tm));
         k_tcgemm<<<dim3(mt, splits), TC_THREADS, smem, st>>>(tm, g);
-        prof_count(c, splits > 1 ? 2 : 1);
+        prof_count(c, splits > 1 ? 3 : 2);
         if (splits > 1) {
             const size_t tot = (size_t)M * nn;
             k_tc_reduce<<<(int)std::min<size_t>((tot + 255) / 256, 4096), 256, 0, st>>>(M, nn, splits, d.splitk,

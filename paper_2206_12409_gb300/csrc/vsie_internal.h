@@ -235,6 +235,9 @@ struct Ctx {
     int64_t pc_ld = 0;                 // its row pitch (complex values, even)
     alignas(64) unsigned char pc_map[128] = {0};   // its TMA tensor map (CUtensorMap)
     int* tc_err = nullptr;             // device flag: a bounded wait of the tensor-core kernel ran out
+    float* pc_bprep = nullptr;         // prepared B' chunks of the tensor-core product
+    size_t pc_bprep_elems = 0;
+    int num_sms = 152;                 // multiprocessors of the context's device
     void* net = nullptr;               // attached learned body preconditioner (not owned)
     float* net_mat = nullptr;          // 2 x n_b: (eps_r - 1) / 50, sigma
     double* net_part = nullptr;        // reduction partials of the network's input scale

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "VSIE_OK", 1: "VSIE_EINVAL", 2: "VSIE_ENOMEM", 3: "VSIE_ECUDA
                 7: "VSIE_EUNSUPPORTED"}
 
 EXPORTS = ["vsie_last_error", "vsie_version", "vsie_setup", "vsie_create", "vsie_sizes",
-           "vsie_matvec", "vsie_rhs_ports", "vsie_rhs_planewave", "vsie_set_loads", "vsie_port_network",
+           "vsie_matvec", "vsie_rhs_ports", "vsie_rhs_planewave", "vsie_rhs_drive", "vsie_set_loads", "vsie_port_network",
            "vsie_solve", "vsie_save", "vsie_load",
            "vsie_get_parts", "vsie_profile", "vsie_profile_query", "vsie_volume_matvec_static",
            "vsie_net_create", "vsie_net_num_params", "vsie_net_set_params", "vsie_net_get_params",
@@ -317,6 +317,20 @@ def vsie_rhs_planewave(ctx, k_hat, e0, B, stream=0):
     kh = (C.c_double * 3)(*[float(v) for v in k_hat])
     ev = (C.c_double * 3)(*[float(v) for v in e0])
     _check(lib.vsie_rhs_planewave(ctx, kh, ev, C.c_void_p(int(B)), C.c_void_p(int(stream))), ctx)
+
+
+def vsie_rhs_drive(ctx, ports, v, B, stream=0):
+    """One column B (device, N double2) with ports[i] driven by the complex voltage v[i]."""
+    vv = np.asarray(v, np.complex128).ravel()
+    pr = (C.c_int32 * max(len(ports), 1))(*[int(x) for x in ports])
+    buf = np.ascontiguousarray(np.stack([vv.real, vv.imag], -1).ravel(), np.float64)
+    _check(load_library().vsie_rhs_drive(ctx, len(ports), pr, _dptr(buf), C.c_void_p(int(B)),
+                                         C.c_void_p(int(stream))), ctx)
+
+
+def cp_mode_voltages(n):
+    """Drive voltages of the circularly polarised mode of an n-loop array (1 V each)."""
+    return np.exp(-2j * np.pi * np.arange(n) / n)
 
 
 def vsie_set_loads(ctx, ports, z_load):
