@@ -454,6 +454,9 @@ constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
 // NL = 2, 4, 8 (M = 224) per CTA with 32 NL threads.
 static const int kXR[] = {8, 16, 32};
 constexpr int kNR = 3;
+// z pass: k_zreg with NL from reg_zNL (variants 0-2), k_zreg_st with NL = 8 (3)
+// and NL = 16 (4, M = 112 only)
+constexpr int kNRZ = 5;
 
 template <typename R>
 static ConvArgs<R> make_args(Ctx& c, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy) {
@@ -528,7 +531,13 @@ static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
     }
     const int R2 = reg_zR2(a);
     if (!R2) return 0;
-    const size_t M = 16 * R2, NL = reg_zNL(R2, rv);
+    const size_t M = 16 * R2;
+    if (rv >= 3) {   // staged kernel: twiddles, exchange, spectrum tile, staging lines
+        const size_t NL = rv == 3 ? 8 : 16;
+        if (a.L1 % NL != 0 || (rv == 4 && R2 != 7)) return 0;
+        return (2 * M + 6 * M * NL + 6 * (size_t)a.Lh3 * NL + 3 * (size_t)a.n3 * NL) * cs;
+    }
+    const size_t NL = reg_zNL(R2, rv);
     return (2 * M + 6 * M * NL) * cs;
 }
 
@@ -552,6 +561,12 @@ static void launch_zreg(const ConvArgs<float>& a, int p, cudaStream_t st) {
     dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
     k_zreg<R2, NL><<<g, 32 * NL, sm, st>>>(a);
 }
+template <int R2, int NL>
+static void launch_zreg_st(const ConvArgs<float>& a, int p, cudaStream_t st) {
+    const size_t sm = reg_smem(a, 2, NL == 8 ? 3 : 4);
+    dim3 g(a.L1 / NL, a.L2, 1);
+    k_zreg_st<R2, NL><<<g, ZStaged<R2, NL>::NT, sm, st>>>(a, p);
+}
 template <int NL>
 static void launch_xyreg(const ConvArgs<float>& a, int p, int pass, cudaStream_t st) {
     if (pass == 0 || pass == 4) {
@@ -565,6 +580,15 @@ static void launch_xyreg(const ConvArgs<float>& a, int p, int pass, cudaStream_t
 static void run_reg_pass(const ConvArgs<float>& a, int p, int pass, int rv, cudaStream_t st) {
     if (pass == 2) {
         const int R2 = reg_zR2(a);
+        if (rv == 3) {
+            if (R2 == 7) launch_zreg_st<7, 8>(a, p, st);
+            else launch_zreg_st<14, 8>(a, p, st);
+            return;
+        }
+        if (rv == 4) {
+            launch_zreg_st<7, 16>(a, p, st);
+            return;
+        }
         if (R2 == 7) {
             if (rv == 0) launch_zreg<7, 4>(a, p, st);
             else if (rv == 1) launch_zreg<7, 8>(a, p, st);
@@ -668,12 +692,17 @@ void conv_autotune(Ctx& c) {
     VSIE_CUDA(cudaEventCreate(&e0));
     VSIE_CUDA(cudaEventCreate(&e1));
     std::string why = "no variant's shared memory fits";
+    // VSIE_ZPASS_VARIANT=v restricts the FP32 z pass to variant v (tests and
+    // tuning sweeps; a variant that does not apply leaves the pass without one)
+    const char* zforce = sizeof(R) == 4 ? std::getenv("VSIE_ZPASS_VARIANT") : nullptr;
+    const int zvar = zforce ? std::atoi(zforce) : -1;
     for (int pass = 0; pass < 5; ++pass) {
         const int ng = pass == 2 ? kNZ : kNX;
-        const int nv = ng + (sizeof(R) == 4 ? kNR : 0);
+        const int nv = ng + (sizeof(R) == 4 ? (pass == 2 ? kNRZ : kNR) : 0);
         float best = 1e30f;
         int bi = -1;
         for (int v = 0; v < nv; ++v) {
+            if (pass == 2 && zvar >= 0 && v != zvar) continue;
             if (v < ng) {
                 const int nl = pass == 2 ? kZV[v].nl : kXV[v].nl;
                 if (smem_of(a, pass, nl) > (size_t)smax) continue;
@@ -753,6 +782,8 @@ void conv_set_attrs() {
         VSIE_ATTR((k_yreg<32, 16, 16, true, false>)); VSIE_ATTR((k_yreg<32, 16, 32, true, false>));
         VSIE_ATTR((k_zreg<7, 4>)); VSIE_ATTR((k_zreg<7, 8>)); VSIE_ATTR((k_zreg<7, 16>));
         VSIE_ATTR((k_zreg<14, 2>)); VSIE_ATTR((k_zreg<14, 4>)); VSIE_ATTR((k_zreg<14, 8>));
+        VSIE_ATTR((k_zreg_st<7, 8>)); VSIE_ATTR((k_zreg_st<7, 16>)); VSIE_ATTR((k_zreg_st<14, 8>));
+        VSIE_CARVE((k_zreg_st<7, 8>)); VSIE_CARVE((k_zreg_st<7, 16>)); VSIE_CARVE((k_zreg_st<14, 8>));
     }
 #undef VSIE_ATTR
 #undef VSIE_CARVE

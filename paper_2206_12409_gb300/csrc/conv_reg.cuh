@@ -241,6 +241,14 @@ __global__ void __launch_bounds__(R2 * NL) k_xinv_reg(ConvArgs<float> a) {
     }
 }
 
+// Exchange rows of 64 bytes (NL = 8 lines) fill half of the 32 banks.  Row m is
+// stored at m ^ ((m >> 4) & 1) and spectrum-tile row r at r ^ ((r >> 1) & 1), so
+// that the four row groups a warp touches at once (rows 16 apart in stage A,
+// 14 apart in the middle phase's stores, 2 apart in the spectrum reads) fall two
+// into each bank half.
+__device__ __forceinline__ int zrow_sw(int m, int nl) { return nl == 8 ? m ^ ((m >> 4) & 1) : m; }
+__device__ __forceinline__ int srow_sw(int r, int nl) { return nl == 8 ? r ^ ((r >> 1) & 1) : r; }
+
 // --------------------------------------------------------------- z pass
 // CTA: NL consecutive k1 columns at one k2, all three components, one RHS;
 // 32 NL threads, one (even/odd half, k1, line) item each in the middle phase.
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(R2 * NL) k_xinv_reg(ConvArgs<float> a) {
 // [component][even/odd][m][line], m in [0, M), reused by both exchanges (the
 // middle phase reads all of it before any thread overwrites it).
 template <int R2, int NL>
-__global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
+__global__ void __launch_bounds__(32 * NL, 16 / NL) k_zreg(ConvArgs<float> a) {
     using C = float2;
     constexpr int M = 16 * R2, L3 = 2 * M, NT = 32 * NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -288,8 +296,9 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
                 we = cmul(we, tt);
                 wo = cmul(wo, tt);
             }
-            de[(t * 16 + k) * NL] = we;
-            dodd[(t * 16 + k) * NL] = wo;
+            const int row = zrow_sw(t * 16 + k, NL);
+            de[row * NL] = we;
+            dodd[row * NL] = wo;
         }
     }
     __syncthreads();
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
         for (int c = 0; c < 3; ++c) {
             const C* src = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
-            for (int t = 0; t < R2; ++t) v[c][t] = src[(t * 16 + k1) * NL];
+            for (int t = 0; t < R2; ++t) v[c][t] = src[zrow_sw(t * 16 + k1, NL) * NL];
         }
         __syncthreads();   // every item has read its inputs; the buffer is reused below
 #pragma unroll
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
             C* dst = ex + (size_t)(c * 2 + half) * M * NL + l;
 #pragma unroll
             for (int n1 = 0; n1 < R2; ++n1)
-                dst[(k1 * R2 + n1) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
+                dst[zrow_sw(k1 * R2 + n1, NL) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
         }
     }
     __syncthreads();
@@ -353,8 +362,9 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
         const C* so = se + (size_t)M * NL;
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1) {
-            e[k1] = se[(k1 * R2 + n1) * NL];
-            o[k1] = so[(k1 * R2 + n1) * NL];
+            const int row = zrow_sw(k1 * R2 + n1, NL);
+            e[k1] = se[row * NL];
+            o[k1] = so[row * NL];
         }
         dftR<true>(e, int_<16>());
         dftR<true>(o, int_<16>());
@@ -365,6 +375,186 @@ __global__ void __launch_bounds__(32 * NL) k_zreg(ConvArgs<float> a) {
                 if (n < a.n3) base[comp * cstride + (size_t)n * plane + k1g] = cadd(e[q], cmulc(o[q], tw[n]));
             }
         }
+    }
+}
+
+// --------------------------------------------------------------- z pass, staged
+// Same transform as k_zreg, reorganised so that the CTA's share of the spectrum
+// and its input lines come from shared memory:
+//   * CTA: NL consecutive k1 columns at one k2, all three components, and every
+//     right-hand side of the launch group in turn (the spectrum tile is loaded
+//     once per CTA, not once per right-hand side);
+//   * the spectrum tile (6 components x (L3/2 + 1) k3 x NL columns) and the
+//     input lines of right-hand side 0 arrive by cp.async at the start; while
+//     right-hand side j is in its middle and final phases, the lines of j + 1
+//     are fetched into the staging buffer, so the global-load latency of
+//     stage A overlaps the arithmetic;
+//   * NT = max(32 NL, 3 R2 NL rounded up to a warp) threads, so stage A and the
+//     final phase take one round (k_zreg needs two at R2 = 14);
+//   * exchange and spectrum rows use the bank swizzle of k_zreg (NL = 8).
+// Shared memory: twiddles (L3), exchange 6 M NL, spectrum 6 (L3/2+1) NL,
+// staging 3 n3 NL complex values.  Needs L1 % NL == 0 (16-byte cp.async).
+template <int R2, int NL> struct ZStaged {
+    static constexpr int M = 16 * R2;
+    static constexpr int NT0 = (3 * R2 * NL + 31) / 32 * 32;
+    static constexpr int NT = NT0 > 32 * NL ? NT0 : 32 * NL;
+    static constexpr int MINB = (R2 == 7 && NL == 8) ? 2 : 1;
+};
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int R2, int NL>
+__global__ void __launch_bounds__(ZStaged<R2, NL>::NT, ZStaged<R2, NL>::MINB) k_zreg_st(ConvArgs<float> a, int p) {
+    using C = float2;
+    constexpr int M = ZStaged<R2, NL>::M, L3 = 2 * M, NT = ZStaged<R2, NL>::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* ex = tw + L3;
+    C* sp = ex + 6 * M * NL;
+    C* pre = sp + (size_t)6 * a.Lh3 * NL;
+    const int k10 = blockIdx.x * NL;
+    const int y = blockIdx.y;
+    const int k2 = y == 0 ? 0 : ((y & 1) ? (y + 1) >> 1 : a.L2 - (y >> 1));
+    const int kk2 = k2 <= a.L2 / 2 ? k2 : a.L2 - k2;
+    const float sg2 = k2 <= a.L2 / 2 ? 1.f : -1.f;
+    const size_t plane = (size_t)a.L2 * a.L1;
+    const size_t cstride = (size_t)a.n3 * plane;
+    const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
+    const size_t st3 = (size_t)a.Lh1 * a.Lh2;
+    for (int i = threadIdx.x; i < L3; i += NT) tw[i] = a.tw3[i];
+    // spectrum tile: row r = c6 Lh3 + kk3, column l
+    for (int e = threadIdx.x; e < 6 * a.Lh3 * NL; e += NT) {
+        const int l = e % NL, r = e / NL;
+        const int c6 = r / a.Lh3, kk3 = r - c6 * a.Lh3;
+        const int k1g = k10 + l;
+        const int kk1 = k1g <= a.L1 / 2 ? k1g : a.L1 - k1g;
+        cpa8(sp + (size_t)srow_sw(r, NL) * NL + l, a.spec + c6 * oct + kk3 * st3 + (size_t)kk2 * a.Lh1 + kk1);
+    }
+    auto prefetch = [&](int j) {
+        const C* src = a.B + (size_t)j * 3 * cstride + (size_t)k2 * a.L1 + k10;
+        for (int e = threadIdx.x; e < 3 * a.n3 * (NL / 2); e += NT) {
+            const int part = e % (NL / 2), row = e / (NL / 2);   // row = comp n3 + n
+            const int comp = row / a.n3, n = row - comp * a.n3;
+            cpa16(pre + (size_t)row * NL + 2 * part, src + comp * cstride + (size_t)n * plane + 2 * part);
+        }
+    };
+    prefetch(0);
+    cpa_commit();
+    const int l1 = threadIdx.x % NL;
+    const int k1g_mid = k10 + l1;
+    const float sg1 = k1g_mid <= a.L1 / 2 ? 1.f : -1.f;
+    for (int j = 0; j < p; ++j) {
+        cpa_wait_all();
+        __syncthreads();   // staged lines of j (and, at j = 0, spectrum and twiddles) are in
+        // forward stage A: even part x[n], odd part x[n] w^n (n < n3 <= M)
+        for (int w = threadIdx.x; w < 3 * R2 * NL; w += NT) {
+            const int l = w % NL, t = (w / NL) % R2, comp = w / (NL * R2);
+            C e[16], o[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int n = t + R2 * q;
+                C x = make_float2(0.f, 0.f);
+                if (n < a.n3) x = pre[(size_t)(comp * a.n3 + n) * NL + l];
+                e[q] = x;
+                o[q] = cmul(x, tw[n]);
+            }
+            dftR<false>(e, int_<16>());
+            dftR<false>(o, int_<16>());
+            C* de = ex + (size_t)(comp * 2) * M * NL + l;
+            C* dodd = de + (size_t)M * NL;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                C we = e[k], wo = o[k];
+                if (k > 0 && t > 0) {
+                    const C tt = tw[2 * t * k];
+                    we = cmul(we, tt);
+                    wo = cmul(wo, tt);
+                }
+                const int row = zrow_sw(t * 16 + k, NL);
+                de[row * NL] = we;
+                dodd[row * NL] = wo;
+            }
+        }
+        __syncthreads();   // exchange written; the staging buffer is free
+        if (j + 1 < p) {
+            prefetch(j + 1);
+            cpa_commit();
+        }
+        // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line)
+        const bool act = threadIdx.x < 32 * NL;
+        const int k1 = (threadIdx.x / NL) % 16, half = threadIdx.x / (16 * NL);
+        C v[3][R2];
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const C* src = ex + (size_t)(c * 2 + half) * M * NL + l1;
+#pragma unroll
+                for (int t = 0; t < R2; ++t) v[c][t] = src[zrow_sw(t * 16 + k1, NL) * NL];
+            }
+        }
+        __syncthreads();   // every item has read its inputs; the buffer is reused below
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dftR<false>(v[c], int_<R2>());
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                const int k3 = 2 * (k1 + 16 * q) + half;
+                const int kk3 = k3 <= L3 / 2 ? k3 : L3 - k3;
+                const float sg3 = k3 <= L3 / 2 ? 1.f : -1.f;
+                const C* so = sp + l1;
+                const C txx = so[(size_t)srow_sw(kk3, NL) * NL];
+                const C tyy = so[(size_t)srow_sw(a.Lh3 + kk3, NL) * NL];
+                const C tzz = so[(size_t)srow_sw(2 * a.Lh3 + kk3, NL) * NL];
+                const C txy = cscale(so[(size_t)srow_sw(3 * a.Lh3 + kk3, NL) * NL], sg1 * sg2);
+                const C txz = cscale(so[(size_t)srow_sw(4 * a.Lh3 + kk3, NL) * NL], sg1 * sg3);
+                const C tyz = cscale(so[(size_t)srow_sw(5 * a.Lh3 + kk3, NL) * NL], sg2 * sg3);
+                const C x = v[0][q], yv = v[1][q], z = v[2][q];
+                C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
+                cfma(ox, txy, yv); cfma(ox, txz, z);
+                cfma(oy, tyy, yv); cfma(oy, tyz, z);
+                cfma(oz, tyz, yv); cfma(oz, tzz, z);
+                v[0][q] = ox; v[1][q] = oy; v[2][q] = oz;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dftR<true>(v[c], int_<R2>());
+                C* dst = ex + (size_t)(c * 2 + half) * M * NL + l1;
+#pragma unroll
+                for (int n1 = 0; n1 < R2; ++n1)
+                    dst[zrow_sw(k1 * R2 + n1, NL) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
+            }
+        }
+        __syncthreads();
+        // inverse stage B (radix 16 over k1) and recombination y[n] = y_e[n] + w^-n y_o[n]
+        C* base = a.B + (size_t)j * 3 * cstride + (size_t)k2 * a.L1;
+        for (int w = threadIdx.x; w < 3 * R2 * NL; w += NT) {
+            const int l = w % NL, n1 = (w / NL) % R2, comp = w / (NL * R2);
+            C e[16], o[16];
+            const C* se = ex + (size_t)(comp * 2) * M * NL + l;
+            const C* so = se + (size_t)M * NL;
+#pragma unroll
+            for (int kq = 0; kq < 16; ++kq) {
+                const int row = zrow_sw(kq * R2 + n1, NL);
+                e[kq] = se[row * NL];
+                o[kq] = so[row * NL];
+            }
+            dftR<true>(e, int_<16>());
+            dftR<true>(o, int_<16>());
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int n = n1 + R2 * q;
+                if (n < a.n3) base[comp * cstride + (size_t)n * plane + k10 + l] = cadd(e[q], cmulc(o[q], tw[n]));
+            }
+        }
+        __syncthreads();   // the exchange buffer is free for the next right-hand side
     }
 }
 

@@ -64,3 +64,16 @@ def test_volume_head_full_size():
     """96 x 96 x 112 head phantom (2 mm), 2 RHS, against the oracle FFT product."""
     g, er, sg = I.layered_head_phantom()
     _check(g, er, sg, 298e6, p=2, ext=(128, 128, 112), off=(16, 16, 0))
+
+
+# z-pass variants of the FP32 operator (the generic half-length Stockham kernels
+# come first, 7 of them; then the register kernels: 7-9 k_zreg, 10 k_zreg_st with
+# 8 lines per CTA, 11 k_zreg_st with 16 lines, M = 112 only)
+@pytest.mark.parametrize("zv", [9, 10, 11])
+def test_volume_head_z_variants(zv, monkeypatch):
+    """Every register z-pass variant on the 2 mm head grid against the oracle
+    (forced through VSIE_ZPASS_VARIANT; 3 RHS, so the staged kernel's loop over
+    right-hand sides and its prefetch run)."""
+    monkeypatch.setenv("VSIE_ZPASS_VARIANT", str(zv))
+    g, er, sg = I.layered_head_phantom()
+    _check(g, er, sg, 298e6, p=3, ext=(128, 128, 112), off=(16, 16, 0))

@@ -13,8 +13,13 @@ from paper_2206_12409_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def test_volume_1mm_sampled_rows_and_precisions():
+@pytest.mark.parametrize("zv", [None, 9, 10])
+def test_volume_1mm_sampled_rows_and_precisions(zv, monkeypatch):
+    """zv: the z-pass variant forced through VSIE_ZPASS_VARIANT (None: tuned);
+    9 is k_zreg with 8 lines per CTA, 10 the staged k_zreg_st."""
     import torch
+    if zv is not None:
+        monkeypatch.setenv("VSIE_ZPASS_VARIANT", str(zv))
     from paper_2206_12409_gb300 import vsie as V
     g, er, sg = I.layered_head_phantom((192, 192, 224), 1e-3)
     f = 298e6
