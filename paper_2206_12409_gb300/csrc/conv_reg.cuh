@@ -110,12 +110,18 @@ __global__ void __launch_bounds__(R2 * NL) k_xfwd_reg(ConvArgs<float> a) {
     for (int i = threadIdx.x; i < L; i += NT) tw[i] = a.tw1[i];
     __syncthreads();
     const C* xb = a.X + (size_t)j * a.ldx + a.xoff + (size_t)comp * a.nb;
+    // the mask byte and the value are loaded independently (no load waits on
+    // another); vacuum voxels are zeroed afterwards
+#pragma unroll 4
     for (int e = threadIdx.x; e < NL * LH; e += NT) {
         const int l = e / LH, i1 = e - l * LH;
         const int q1 = i1 - a.o1;
         const int64_t lb = lbase[l];
         C v = make_float2(0.f, 0.f);
-        if (lb >= 0 && q1 >= 0 && q1 < a.b1 && a.mask[lb + q1]) v = xb[lb + q1];
+        if (lb >= 0 && q1 >= 0 && q1 < a.b1) {
+            const C x = xb[lb + q1];
+            v = a.mask[lb + q1] ? x : v;
+        }
         sx[l * (LH + 1) + i1] = v;
     }
     __syncthreads();
