@@ -301,7 +301,8 @@ VSIE_API vsie_status vsie_profile_query(vsie_ctx* ctx, int32_t group, double* ms
 /* Body block only, y_b = Z_bb x_b, without allocating anything (this library
  * has no counterpart of it in the paper).  For callers that cannot allocate
  * device memory while the operator runs (a fixed memory pool that must not
- * grow, a real-time loop, code being recorded into a CUDA graph).  X and Y hold
+ * grow, a real-time loop that may not wait on the allocator, a host runtime
+ * that owns all device memory itself).  X and Y hold
  * p body vectors of 3 n_b complex values each (component-major, device,
  * leading dimensions >= 3 n_b).  Vacuum voxels return their input.
  * The FFT work space comes from one file-scope device array of 32 MiB that

@@ -2,8 +2,8 @@
 //
 // Some callers cannot allocate device memory while they run this operator: a
 // solver whose memory is owned by a fixed pool that must not grow, a real-time
-// loop that may not block on the allocator, or code that is being recorded
-// into a CUDA graph, where a new cudaMalloc would break the capture.  For them
+// loop that may not block on the allocator, or a host runtime that hands out
+// all device memory itself.  For them
 // the two FFT work buffers of the fused convolution live in one file-scope
 // device array of fixed size instead of in per-context allocations.  Every GPU
 // that loads this library holds that array until the process exits.

@@ -2,7 +2,7 @@
 ordinary matvec.
 
 Callers that cannot allocate device memory while the operator runs (fixed
-memory pools, real-time loops, code recorded into CUDA graphs) use that entry
+memory pools, real-time loops, runtimes that own all device memory) use that entry
 point; its FFT work space is a fixed 32 MiB device array inside the library.
 This file is collected last so that a failure here comes after every other
 test has run."""
