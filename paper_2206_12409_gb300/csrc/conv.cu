@@ -454,9 +454,10 @@ constexpr int kNZ = sizeof(kZV) / sizeof(kZV[0]);
 // NL = 2, 4, 8 (M = 224) per CTA with 32 NL threads.
 static const int kXR[] = {8, 16, 32};
 constexpr int kNR = 3;
-// z pass: k_zreg with NL from reg_zNL (variants 0-2), k_zreg_st with NL = 8 (3)
-// and NL = 16 (4, M = 112 only)
-constexpr int kNRZ = 5;
+// z pass: k_zreg with NL from reg_zNL (variants 0-2), k_zreg_st with NL = 8 (3),
+// NL = 16 (4, M = 112 only) and NL = 8 with the thread-pair middle phase (5,
+// M = 224 only)
+constexpr int kNRZ = 6;
 
 template <typename R>
 static ConvArgs<R> make_args(Ctx& c, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy) {
@@ -533,8 +534,8 @@ static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
     if (!R2) return 0;
     const size_t M = 16 * R2;
     if (rv >= 3) {   // staged kernel: twiddles, exchange, spectrum tile, staging lines
-        const size_t NL = rv == 3 ? 8 : 16;
-        if (a.L1 % NL != 0 || (rv == 4 && R2 != 7)) return 0;
+        const size_t NL = rv == 4 ? 16 : 8;
+        if (a.L1 % NL != 0 || (rv == 4 && R2 != 7) || (rv == 5 && R2 != 14)) return 0;
         return (2 * M + 6 * M * NL + 6 * (size_t)a.Lh3 * NL + 3 * (size_t)a.n3 * NL) * cs;
     }
     const size_t NL = reg_zNL(R2, rv);
@@ -561,11 +562,11 @@ static void launch_zreg(const ConvArgs<float>& a, int p, cudaStream_t st) {
     dim3 g((a.L1 + NL - 1) / NL, a.L2, p);
     k_zreg<R2, NL><<<g, 32 * NL, sm, st>>>(a);
 }
-template <int R2, int NL>
+template <int R2, int NL, bool SPLIT = false>
 static void launch_zreg_st(const ConvArgs<float>& a, int p, cudaStream_t st) {
-    const size_t sm = reg_smem(a, 2, NL == 8 ? 3 : 4);
+    const size_t sm = reg_smem(a, 2, SPLIT ? 5 : NL == 8 ? 3 : 4);
     dim3 g(a.L1 / NL, a.L2, 1);
-    k_zreg_st<R2, NL><<<g, ZStaged<R2, NL>::NT, sm, st>>>(a, p);
+    k_zreg_st<R2, NL, SPLIT><<<g, ZStaged<R2, NL, SPLIT>::NT, sm, st>>>(a, p);
 }
 template <int NL>
 static void launch_xyreg(const ConvArgs<float>& a, int p, int pass, cudaStream_t st) {
@@ -587,6 +588,10 @@ static void run_reg_pass(const ConvArgs<float>& a, int p, int pass, int rv, cuda
         }
         if (rv == 4) {
             launch_zreg_st<7, 16>(a, p, st);
+            return;
+        }
+        if (rv == 5) {
+            launch_zreg_st<14, 8, true>(a, p, st);
             return;
         }
         if (R2 == 7) {
@@ -782,8 +787,10 @@ void conv_set_attrs() {
         VSIE_ATTR((k_yreg<32, 16, 16, true, false>)); VSIE_ATTR((k_yreg<32, 16, 32, true, false>));
         VSIE_ATTR((k_zreg<7, 4>)); VSIE_ATTR((k_zreg<7, 8>)); VSIE_ATTR((k_zreg<7, 16>));
         VSIE_ATTR((k_zreg<14, 2>)); VSIE_ATTR((k_zreg<14, 4>)); VSIE_ATTR((k_zreg<14, 8>));
-        VSIE_ATTR((k_zreg_st<7, 8>)); VSIE_ATTR((k_zreg_st<7, 16>)); VSIE_ATTR((k_zreg_st<14, 8>));
-        VSIE_CARVE((k_zreg_st<7, 8>)); VSIE_CARVE((k_zreg_st<7, 16>)); VSIE_CARVE((k_zreg_st<14, 8>));
+        VSIE_ATTR((k_zreg_st<7, 8, false>)); VSIE_ATTR((k_zreg_st<7, 16, false>));
+        VSIE_ATTR((k_zreg_st<14, 8, false>)); VSIE_ATTR((k_zreg_st<14, 8, true>));
+        VSIE_CARVE((k_zreg_st<7, 8, false>)); VSIE_CARVE((k_zreg_st<7, 16, false>));
+        VSIE_CARVE((k_zreg_st<14, 8, false>)); VSIE_CARVE((k_zreg_st<14, 8, true>));
     }
 #undef VSIE_ATTR
 #undef VSIE_CARVE

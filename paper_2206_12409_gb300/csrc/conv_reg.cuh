@@ -400,11 +400,12 @@ __global__ void __launch_bounds__(32 * NL, 16 / NL) k_zreg(ConvArgs<float> a) {
 //   * exchange and spectrum rows use the bank swizzle of k_zreg (NL = 8).
 // Shared memory: twiddles (L3), exchange 6 M NL, spectrum 6 (L3/2+1) NL,
 // staging 3 n3 NL complex values.  Needs L1 % NL == 0 (16-byte cp.async).
-template <int R2, int NL> struct ZStaged {
+template <int R2, int NL, bool SPLIT = false> struct ZStaged {
     static constexpr int M = 16 * R2;
     static constexpr int NT0 = (3 * R2 * NL + 31) / 32 * 32;
-    static constexpr int NT = NT0 > 32 * NL ? NT0 : 32 * NL;
-    static constexpr int MINB = (R2 == 7 && NL == 8) ? 2 : 1;
+    static constexpr int NMID = (SPLIT ? 64 : 32) * NL;   // threads of the middle phase
+    static constexpr int NT = NT0 > NMID ? NT0 : NMID;
+    static constexpr int MINB = (R2 == 7 && NL == 8 && !SPLIT) ? 2 : 1;
 };
 __device__ __forceinline__ void cpa8(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -417,10 +418,12 @@ __device__ __forceinline__ void cpa16(void* dst, const void* src) {
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <int R2, int NL>
-__global__ void __launch_bounds__(ZStaged<R2, NL>::NT, ZStaged<R2, NL>::MINB) k_zreg_st(ConvArgs<float> a, int p) {
+template <int R2, int NL, bool SPLIT>
+__global__ void __launch_bounds__(ZStaged<R2, NL, SPLIT>::NT, ZStaged<R2, NL, SPLIT>::MINB)
+    k_zreg_st(ConvArgs<float> a, int p) {
     using C = float2;
-    constexpr int M = ZStaged<R2, NL>::M, L3 = 2 * M, NT = ZStaged<R2, NL>::NT;
+    constexpr int M = ZStaged<R2, NL, SPLIT>::M, L3 = 2 * M, NT = ZStaged<R2, NL, SPLIT>::NT;
+    static_assert(!SPLIT || (R2 % 2 == 0 && NT == 64 * NL), "split middle phase: even R2, one thread pair per item");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* ex = tw + L3;
@@ -494,33 +497,93 @@ __global__ void __launch_bounds__(ZStaged<R2, NL>::NT, ZStaged<R2, NL>::MINB) k_
             prefetch(j + 1);
             cpa_commit();
         }
-        // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line)
-        const bool act = threadIdx.x < 32 * NL;
-        const int k1 = (threadIdx.x / NL) % 16, half = threadIdx.x / (16 * NL);
-        C v[3][R2];
-        if (act) {
+        if constexpr (!SPLIT) {
+            // forward stage B, spectrum multiply, inverse stage A: item (half, k1, line)
+            const bool act = threadIdx.x < 32 * NL;
+            const int k1 = (threadIdx.x / NL) % 16, half = threadIdx.x / (16 * NL);
+            C v[3][R2];
+            if (act) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const C* src = ex + (size_t)(c * 2 + half) * M * NL + l1;
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) v[c][t] = src[zrow_sw(t * 16 + k1, NL) * NL];
+                }
+            }
+            __syncthreads();   // every item has read its inputs; the buffer is reused below
+            if (act) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dftR<false>(v[c], int_<R2>());
+#pragma unroll
+                for (int q = 0; q < R2; ++q) {
+                    const int k3 = 2 * (k1 + 16 * q) + half;
+                    const int kk3 = k3 <= L3 / 2 ? k3 : L3 - k3;
+                    const float sg3 = k3 <= L3 / 2 ? 1.f : -1.f;
+                    const C* so = sp + l1;
+                    const C txx = so[(size_t)srow_sw(kk3, NL) * NL];
+                    const C tyy = so[(size_t)srow_sw(a.Lh3 + kk3, NL) * NL];
+                    const C tzz = so[(size_t)srow_sw(2 * a.Lh3 + kk3, NL) * NL];
+                    const C txy = cscale(so[(size_t)srow_sw(3 * a.Lh3 + kk3, NL) * NL], sg1 * sg2);
+                    const C txz = cscale(so[(size_t)srow_sw(4 * a.Lh3 + kk3, NL) * NL], sg1 * sg3);
+                    const C tyz = cscale(so[(size_t)srow_sw(5 * a.Lh3 + kk3, NL) * NL], sg2 * sg3);
+                    const C x = v[0][q], yv = v[1][q], z = v[2][q];
+                    C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
+                    cfma(ox, txy, yv); cfma(ox, txz, z);
+                    cfma(oy, tyy, yv); cfma(oy, tyz, z);
+                    cfma(oz, tyz, yv); cfma(oz, tzz, z);
+                    v[0][q] = ox; v[1][q] = oy; v[2][q] = oz;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    dftR<true>(v[c], int_<R2>());
+                    C* dst = ex + (size_t)(c * 2 + half) * M * NL + l1;
+#pragma unroll
+                    for (int n1 = 0; n1 < R2; ++n1)
+                        dst[zrow_sw(k1 * R2 + n1, NL) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
+                }
+            }
+        } else {
+            // the same phase with every item on a pair of adjacent lanes: lane sub
+            // takes the samples t = 2m + sub, so the radix-R2 transforms become two
+            // radix-R2/2 halves joined by one shuffle exchange each way, and each lane
+            // holds 3 x R2/2 values (half the registers, twice the threads)
+            constexpr int RH = R2 / 2, WS = L3 / R2;   // tw[WS q] = exp(-2 pi i q / R2)
+            const int it = threadIdx.x >> 1, sub = threadIdx.x & 1;
+            const int lm = it % NL, k1 = (it / NL) % 16, half = it / (16 * NL);
+            const float sg1m = k10 + lm <= a.L1 / 2 ? 1.f : -1.f;
+            C v[3][RH];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const C* src = ex + (size_t)(c * 2 + half) * M * NL + l1;
+                const C* src = ex + (size_t)(c * 2 + half) * M * NL + lm;
 #pragma unroll
-                for (int t = 0; t < R2; ++t) v[c][t] = src[zrow_sw(t * 16 + k1, NL) * NL];
+                for (int m = 0; m < RH; ++m) v[c][m] = src[zrow_sw((2 * m + sub) * 16 + k1, NL) * NL];
             }
-        }
-        __syncthreads();   // every item has read its inputs; the buffer is reused below
-        if (act) {
+            __syncthreads();   // every item has read its inputs; the buffer is reused below
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dftR<false>(v[c], int_<R2>());
+            for (int c = 0; c < 3; ++c) {
+                dftR<false>(v[c], int_<RH>());   // sub 0: E[q], sub 1: O[q]
 #pragma unroll
-            for (int q = 0; q < R2; ++q) {
-                const int k3 = 2 * (k1 + 16 * q) + half;
+                for (int q = 0; q < RH; ++q) {
+                    C pv;
+                    pv.x = __shfl_xor_sync(0xffffffffu, v[c][q].x, 1);
+                    pv.y = __shfl_xor_sync(0xffffffffu, v[c][q].y, 1);
+                    const C e = sub ? pv : v[c][q];
+                    C o = sub ? v[c][q] : pv;
+                    if (q > 0) o = cmul(o, tw[WS * q]);
+                    v[c][q] = sub ? csub(e, o) : cadd(e, o);   // X[q + RH sub]
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RH; ++q) {
+                const int k3 = 2 * (k1 + 16 * (q + RH * sub)) + half;
                 const int kk3 = k3 <= L3 / 2 ? k3 : L3 - k3;
                 const float sg3 = k3 <= L3 / 2 ? 1.f : -1.f;
-                const C* so = sp + l1;
+                const C* so = sp + lm;
                 const C txx = so[(size_t)srow_sw(kk3, NL) * NL];
                 const C tyy = so[(size_t)srow_sw(a.Lh3 + kk3, NL) * NL];
                 const C tzz = so[(size_t)srow_sw(2 * a.Lh3 + kk3, NL) * NL];
-                const C txy = cscale(so[(size_t)srow_sw(3 * a.Lh3 + kk3, NL) * NL], sg1 * sg2);
-                const C txz = cscale(so[(size_t)srow_sw(4 * a.Lh3 + kk3, NL) * NL], sg1 * sg3);
+                const C txy = cscale(so[(size_t)srow_sw(3 * a.Lh3 + kk3, NL) * NL], sg1m * sg2);
+                const C txz = cscale(so[(size_t)srow_sw(4 * a.Lh3 + kk3, NL) * NL], sg1m * sg3);
                 const C tyz = cscale(so[(size_t)srow_sw(5 * a.Lh3 + kk3, NL) * NL], sg2 * sg3);
                 const C x = v[0][q], yv = v[1][q], z = v[2][q];
                 C ox = cmul(txx, x), oy = cmul(txy, x), oz = cmul(txz, x);
@@ -531,11 +594,27 @@ __global__ void __launch_bounds__(ZStaged<R2, NL>::NT, ZStaged<R2, NL>::MINB) k_
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                dftR<true>(v[c], int_<R2>());
-                C* dst = ex + (size_t)(c * 2 + half) * M * NL + l1;
+                // inverse by decimation in frequency: even outputs from X[q] + X[q + RH],
+                // odd outputs from (X[q] - X[q + RH]) exp(+2 pi i q / R2)
 #pragma unroll
-                for (int n1 = 0; n1 < R2; ++n1)
-                    dst[zrow_sw(k1 * R2 + n1, NL) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][n1], tw[2 * n1 * k1]) : v[c][n1];
+                for (int q = 0; q < RH; ++q) {
+                    C pv;
+                    pv.x = __shfl_xor_sync(0xffffffffu, v[c][q].x, 1);
+                    pv.y = __shfl_xor_sync(0xffffffffu, v[c][q].y, 1);
+                    if (sub == 0) {
+                        v[c][q] = cadd(v[c][q], pv);
+                    } else {
+                        const C d = csub(pv, v[c][q]);
+                        v[c][q] = q > 0 ? cmulc(d, tw[WS * q]) : d;
+                    }
+                }
+                dftR<true>(v[c], int_<RH>());   // v[c][m]: output n1 = 2 m + sub
+                C* dst = ex + (size_t)(c * 2 + half) * M * NL + lm;
+#pragma unroll
+                for (int m = 0; m < RH; ++m) {
+                    const int n1 = 2 * m + sub;
+                    dst[zrow_sw(k1 * R2 + n1, NL) * NL] = (n1 > 0 && k1 > 0) ? cmulc(v[c][m], tw[2 * n1 * k1]) : v[c][m];
+                }
             }
         }
         __syncthreads();

@@ -13,10 +13,11 @@ from paper_2206_12409_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("zv", [None, 9, 10])
+@pytest.mark.parametrize("zv", [None, 9, 10, 12])
 def test_volume_1mm_sampled_rows_and_precisions(zv, monkeypatch):
     """zv: the z-pass variant forced through VSIE_ZPASS_VARIANT (None: tuned);
-    9 is k_zreg with 8 lines per CTA, 10 the staged k_zreg_st."""
+    9 is k_zreg with 8 lines per CTA, 10 the staged k_zreg_st, 12 the staged kernel
+    with its middle phase on thread pairs."""
     import torch
     if zv is not None:
         monkeypatch.setenv("VSIE_ZPASS_VARIANT", str(zv))
