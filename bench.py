@@ -67,8 +67,9 @@ def _conv_source_hash():
 def _traffic_per_launch(p):
     """DRAM bytes per K1 launch group of p right-hand sides from the committed ncu
     summary of the 1 mm grid, or None when the kernel sources changed since the
-    counters were taken.  The summary holds the bytes of one right-hand side; the
-    passes move data in proportion to p."""
+    counters were taken.  The summary holds the bytes that scale with the
+    right-hand sides (per RHS) and those read once per launch group (the spectrum
+    octants of the staged z pass)."""
     path = os.path.join(ROOT, "profiles", "fft_conv_1mm_grid.md")
     if not os.path.exists(path):
         return None
@@ -81,7 +82,7 @@ def _traffic_per_launch(p):
     if vals.get("source_hash") != _conv_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_rhs"]) * p
+        return float(vals["dram_bytes_per_rhs"]) * p + float(vals.get("dram_bytes_per_group", 0))
     except (KeyError, ValueError):
         return None
 

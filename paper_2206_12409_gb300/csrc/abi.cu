@@ -259,9 +259,19 @@ static void init_ctx(Ctx& c, const vsie_grid* body, const double* eps_r, const d
     c.s = parts && parts->stencil > 0 ? parts->stencil : 3;
     const int s = c.s, s3 = s * s * s;
     std::vector<int32_t> flags((size_t)c.ne[1] * c.ne[2], 0);
+    // bit 1: the line crosses the body grid; bit 4: it holds a material voxel (its
+    // x-forward transform can be non-zero); bit 2 (below): coil grid points
     for (int i3 = 0; i3 < c.nb[2]; ++i3)
-        for (int i2 = 0; i2 < c.nb[1]; ++i2)
-            flags[(i2 + c.off[1]) + (size_t)c.ne[1] * (i3 + c.off[2])] |= 1;
+        for (int i2 = 0; i2 < c.nb[1]; ++i2) {
+            int32_t& f = flags[(i2 + c.off[1]) + (size_t)c.ne[1] * (i3 + c.off[2])];
+            f |= 1;
+            const size_t b0 = (size_t)c.nb[0] * (i2 + (size_t)c.nb[1] * i3);
+            for (int i1 = 0; i1 < c.nb[0]; ++i1)
+                if (mask[b0 + i1]) {
+                    f |= 4;
+                    break;
+                }
+        }
     std::vector<int32_t> lptr((size_t)c.ne[1] * c.ne[2] + 1, 0), li1, lci;
     if (c.m_n > 0) {
         if (!parts->W || !parts->base || !parts->Znn)

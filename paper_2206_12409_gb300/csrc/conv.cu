@@ -51,6 +51,13 @@ struct ConvArgs {
     int zhalf;      // 1: the Z pass runs on half-length transforms
 };
 
+// line flags (per (i2, i3) line of the extended grid): 1 crosses the body grid,
+// 2 holds coil grid points, 4 holds a material voxel.  A line without 2 or 4 has a
+// zero x-forward transform: the x-forward passes do not store it, the y-forward
+// passes read it as zero, and the y-inverse passes do not store it (the x-inverse
+// epilogue uses the transform of a line only through bits 2 and 4).
+constexpr int kLineLive = 6;
+
 // x / d given magic = magic_div(d); magic 0 encodes d == 1
 __device__ __forceinline__ int udiv(int x, uint32_t magic) {
     return magic ? (int)__umulhi((uint32_t)x, magic) : x;
@@ -138,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_xfwd(ConvArgs<R> a) {
     const int nvalid = min(NL, nlines - lin0) * a.L1;
     for (int e = threadIdx.x; e < nvalid; e += blockDim.x) {
         const int l = udiv(e, a.L1magic), k = e - l * a.L1;
-        out[e] = res[k * KS + l];
+        if (a.line_flag[lin0 + l] & kLineLive) out[e] = res[k * KS + l];   // zero lines are not stored
     }
 }
 
@@ -156,6 +163,10 @@ __global__ void __launch_bounds__(1024) k_ypass(ConvArgs<R> a) {
     const int nout = INV ? a.n2 : a.L2;    // rows written
     const C* in = INV ? a.B + ((size_t)ja * a.n3 + i3) * a.L2 * a.L1
                       : a.A + ((size_t)ja * a.n3 + i3) * a.n2 * a.L1;
+    // rows i2 whose x line is zero: not read (forward), not written (inverse)
+    int* rowf = reinterpret_cast<int*>(scr + (size_t)a.L2 * NL);
+    for (int i = threadIdx.x; i < a.n2; i += blockDim.x) rowf[i] = a.line_flag[i + a.n2 * i3] & kLineLive;
+    __syncthreads();
     constexpr int U = 8;
     const int tot = NL * a.L2;
     for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
@@ -166,7 +177,7 @@ __global__ void __launch_bounds__(1024) k_ypass(ConvArgs<R> a) {
             const int l = e % NL, row = e / NL;
             const int k1 = k10 + l;
             v[u] = czero<C>();
-            if (e < tot && row < nin && k1 < a.L1) v[u] = in[(size_t)row * a.L1 + k1];
+            if (e < tot && row < nin && k1 < a.L1 && (INV || rowf[row])) v[u] = in[(size_t)row * a.L1 + k1];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -181,7 +192,7 @@ __global__ void __launch_bounds__(1024) k_ypass(ConvArgs<R> a) {
     for (int e = threadIdx.x; e < NL * nout; e += blockDim.x) {
         const int l = e % NL, row = e / NL;
         const int k1 = k10 + l;
-        if (k1 < a.L1) out[(size_t)row * a.L1 + k1] = res[e];
+        if (k1 < a.L1 && (!INV || rowf[row])) out[(size_t)row * a.L1 + k1] = res[e];
     }
 }
 
@@ -398,7 +409,8 @@ __global__ void __launch_bounds__(1024) k_xinv(ConvArgs<R> a) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * blockDim.x;
-            v[u] = e < nvalid ? in[e] : czero<C>();
+            v[u] = czero<C>();
+            if (e < nvalid && (lflag[udiv(e, a.L1magic)] & kLineLive)) v[u] = in[e];   // zero lines were not stored
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -494,7 +506,7 @@ static void launch_x(const ConvArgs<R>& a, int p, int t, bool inv, cudaStream_t 
 }
 template <typename R, int NL>
 static void launch_y(const ConvArgs<R>& a, int p, int t, bool inv, cudaStream_t st) {
-    const size_t sm = (size_t)a.L2 * (2 * NL + 1) * sizeof(cx<R>);
+    const size_t sm = (size_t)a.L2 * (2 * NL + 1) * sizeof(cx<R>) + (size_t)a.n2 * sizeof(int);
     dim3 g((a.L1 + NL - 1) / NL, a.n3, 3 * p);
     if (inv) k_ypass<R, NL, true><<<g, t, sm, st>>>(a);
     else k_ypass<R, NL, false><<<g, t, sm, st>>>(a);
@@ -528,7 +540,7 @@ static size_t reg_smem(const ConvArgs<float>& a, int pass, int rv) {
     }
     if (pass == 1 || pass == 3) {
         if (!reg_len_ok(a.L2)) return 0;
-        return ((size_t)a.L2 + (size_t)kXR[rv] * a.L2) * cs;
+        return ((size_t)a.L2 + (size_t)kXR[rv] * a.L2) * cs + (size_t)a.n2 * sizeof(int);
     }
     const int R2 = reg_zR2(a);
     if (!R2) return 0;
@@ -551,7 +563,7 @@ static void launch_xreg(const ConvArgs<float>& a, int p, bool inv, cudaStream_t 
 }
 template <int R1, int NL>
 static void launch_yreg(const ConvArgs<float>& a, int p, bool inv, cudaStream_t st) {
-    const size_t sm = ((size_t)a.L2 + (size_t)NL * a.L2) * sizeof(float2);
+    const size_t sm = ((size_t)a.L2 + (size_t)NL * a.L2) * sizeof(float2) + (size_t)a.n2 * sizeof(int);
     dim3 g((a.L1 + NL - 1) / NL, a.n3, 3 * p);
     if (inv) k_yreg<R1, 16, NL, true, false><<<g, 16 * NL, sm, st>>>(a);
     else k_yreg<R1, 16, NL, false, true><<<g, 16 * NL, sm, st>>>(a);
@@ -616,7 +628,7 @@ template <typename R>
 static size_t smem_of(const ConvArgs<R>& a, int pass, int nl) {
     const size_t cs = sizeof(cx<R>);
     if (pass == 0 || pass == 4) return (size_t)a.L1 * (2 * nl + 3) * cs;
-    if (pass == 1 || pass == 3) return (size_t)a.L2 * (2 * nl + 1) * cs;
+    if (pass == 1 || pass == 3) return (size_t)a.L2 * (2 * nl + 1) * cs + (size_t)a.n2 * sizeof(int);
     return (size_t)a.L3 * (6 * nl + 1) * cs;
 }
 

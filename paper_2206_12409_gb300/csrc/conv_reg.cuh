@@ -38,7 +38,11 @@ __global__ void __launch_bounds__(R2 * NL) k_yreg(ConvArgs<float> a) {
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* ex = tw + L;
     const int k10 = blockIdx.x * NL, i3 = blockIdx.y, ja = blockIdx.z;
+    // rows i2 whose x line is zero: not read (forward), not written (inverse)
+    int* rowf = reinterpret_cast<int*>(ex + (size_t)L * NL);
+    for (int i = threadIdx.x; i < a.n2; i += NT) rowf[i] = a.line_flag[i + a.n2 * i3] & kLineLive;
     for (int i = threadIdx.x; i < L; i += NT) tw[i] = a.tw2[i];
+    __syncthreads();
     const int nin = INV ? L : a.n2;
     const int nout = INV ? a.n2 : L;
     const size_t pl = (size_t)ja * a.n3 + i3;
@@ -52,7 +56,8 @@ __global__ void __launch_bounds__(R2 * NL) k_yreg(ConvArgs<float> a) {
         for (int j = 0; j < R1; ++j) {
             const int row = t + R2 * j;
             v[j] = make_float2(0.f, 0.f);
-            if (!(HZ && j >= R1 / 2) && row < nin && k1g < a.L1) v[j] = in[(size_t)row * a.L1 + k1g];
+            if (!(HZ && j >= R1 / 2) && row < nin && k1g < a.L1 && (INV || rowf[row]))
+                v[j] = in[(size_t)row * a.L1 + k1g];
         }
         __syncthreads();   // twiddles loaded
         dftR<INV>(v, int_<R1>());
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(R2 * NL) k_yreg(ConvArgs<float> a) {
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) {
                 const int row = k1 + R1 * k2;
-                if (row < nout) out[(size_t)row * a.L1 + k1g] = v[k2];
+                if (row < nout && (!INV || rowf[row])) out[(size_t)row * a.L1 + k1g] = v[k2];
             }
         }
     }
@@ -94,9 +99,11 @@ __global__ void __launch_bounds__(R2 * NL) k_xfwd_reg(ConvArgs<float> a) {
     C* sx = tw + L;
     C* ex = sx + NL * (LH + 1);
     __shared__ int64_t lbase[NL];
+    __shared__ int llive[NL];
     const int comp = blockIdx.y, j = blockIdx.z;
     const int nlines = a.n2 * a.n3;
     const int lin0 = blockIdx.x * NL;
+    int live = 0;
     if (threadIdx.x < NL) {
         const int lin = lin0 + threadIdx.x;
         int64_t b = -1;
@@ -104,11 +111,13 @@ __global__ void __launch_bounds__(R2 * NL) k_xfwd_reg(ConvArgs<float> a) {
             const int i3 = udiv(lin, a.n2magic), i2 = lin - i3 * a.n2;
             const int q2 = i2 - a.o2, q3 = i3 - a.o3;
             if (q2 >= 0 && q2 < a.b2 && q3 >= 0 && q3 < a.b3) b = (int64_t)a.b1 * (q2 + (int64_t)a.b2 * q3);
+            live = a.line_flag[lin] & kLineLive;
         }
         lbase[threadIdx.x] = b;
+        llive[threadIdx.x] = live;
     }
     for (int i = threadIdx.x; i < L; i += NT) tw[i] = a.tw1[i];
-    __syncthreads();
+    if (!__syncthreads_or(live)) return;   // every line of this CTA is zero: nothing to store
     const C* xb = a.X + (size_t)j * a.ldx + a.xoff + (size_t)comp * a.nb;
     // the mask byte and the value are loaded independently (no load waits on
     // another); vacuum voxels are zeroed afterwards
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(R2 * NL) k_xfwd_reg(ConvArgs<float> a) {
 #pragma unroll
         for (int t = 0; t < R2; ++t) v[t] = ex[l * XS + t * (R1 + 1) + k1];
         dftR<false>(v, int_<R2>());
-        if (lin0 + l < nlines) {
+        if (lin0 + l < nlines && llive[l]) {
 #pragma unroll
             for (int k2 = 0; k2 < R2; ++k2) out[(size_t)l * L + k1 + R1 * k2] = v[k2];
         }
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(R2 * NL) k_xinv_reg(ConvArgs<float> a) {
     const C* in = a.A + (((size_t)j * 3 + comp) * nlines + lin0) * L;
     {
         const int t = threadIdx.x % R2, l = threadIdx.x / R2;
-        const bool ok = lin0 + l < nlines;
+        const bool ok = lin0 + l < nlines && (lflag[l] & kLineLive);   // zero lines were not stored
         C v[R1];
 #pragma unroll
         for (int jj = 0; jj < R1; ++jj) v[jj] = ok ? in[(size_t)l * L + t + R2 * jj] : make_float2(0.f, 0.f);
