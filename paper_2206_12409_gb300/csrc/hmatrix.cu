@@ -369,22 +369,29 @@ __global__ void __launch_bounds__(256) k_hm_vt(int m, int p, const int* __restri
     }
 }
 
-// One CTA per leaf row cluster: rows [rs, re) in cluster order, one thread per row.
+// One CTA per leaf row cluster: rows [rs, re) in cluster order.  The CTA has ng
+// groups of rt threads (rt = the largest leaf, a warp multiple); thread r of group g
+// owns row r and the columns jj = g, g + ng, ... of every staged chunk, so ng loads
+// of each row are in flight at once.  The ng partial sums are added in a fixed
+// order at the end (group 0 takes those of groups 1, 2, ... in turn).
+// Dynamic shared memory: max(kHmStage, rt) x NB complex values.
+constexpr int kHmStage = 128;   // columns staged per step
 template <typename R, int NB>
-__global__ void __launch_bounds__(256) k_hm_rows(int m, int p, const int* __restrict__ perm,
-                                                 const int* __restrict__ rl, const int* __restrict__ eptr,
-                                                 const int* __restrict__ eblk, const int* __restrict__ eroff,
-                                                 const int4* __restrict__ blk, const int* __restrict__ kb,
-                                                 const int64_t* __restrict__ doff, const cx<R>* __restrict__ D,
-                                                 const cx<R>* __restrict__ U, const int* __restrict__ toff,
-                                                 const cx<R>* __restrict__ t, const cx<R>* __restrict__ xt,
-                                                 cx<R>* __restrict__ Y, int64_t ldy) {
+__global__ void __launch_bounds__(512) k_hm_rows(int m, int p, const int* __restrict__ perm,
+                                                  const int* __restrict__ rl, const int* __restrict__ eptr,
+                                                  const int* __restrict__ eblk, const int* __restrict__ eroff,
+                                                  const int4* __restrict__ blk, const int* __restrict__ kb,
+                                                  const int64_t* __restrict__ doff, const cx<R>* __restrict__ D,
+                                                  const cx<R>* __restrict__ U, const int* __restrict__ toff,
+                                                  const cx<R>* __restrict__ t, const cx<R>* __restrict__ xt,
+                                                  cx<R>* __restrict__ Y, int64_t ldy, int rt) {
     using C = cx<R>;
-    constexpr int CH = 64;   // columns staged per chunk
-    __shared__ C sx[CH * NB];
+    extern __shared__ __align__(16) unsigned char hm_smem[];
+    C* sx = reinterpret_cast<C*>(hm_smem);
     const int L = blockIdx.x;
     const int rs = rl[L], nr = rl[L + 1] - rs;
-    const int r = threadIdx.x;
+    const int ng = blockDim.x / rt;
+    const int grp = threadIdx.x / rt, r = threadIdx.x - grp * rt;
     C acc[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) acc[c] = czero<C>();
@@ -394,8 +401,8 @@ __global__ void __launch_bounds__(256) k_hm_rows(int m, int p, const int* __rest
         const int k = kb[b];
         const C* Ab = (k < 0 ? D : U) + doff[b];
         const int ncol = k < 0 ? B.w : k;
-        for (int j0 = 0; j0 < ncol; j0 += CH) {
-            const int nj = min(CH, ncol - j0);
+        for (int j0 = 0; j0 < ncol; j0 += kHmStage) {
+            const int nj = min(kHmStage, ncol - j0);
             __syncthreads();
             for (int q = threadIdx.x; q < nj * NB; q += blockDim.x) {
                 const int jj = q / NB, c = q - jj * NB;
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(256) k_hm_rows(int m, int p, const int* __rest
             __syncthreads();
             if (r < nr) {
                 const C* a = Ab + (size_t)(ro + r) + (size_t)B.y * j0;
-                for (int jj = 0; jj < nj; ++jj) {
+                for (int jj = grp; jj < nj; jj += ng) {
                     const C av = a[(size_t)B.y * jj];
 #pragma unroll
                     for (int c = 0; c < NB; ++c) cfma(acc[c], av, sx[jj * NB + c]);
@@ -414,7 +421,19 @@ __global__ void __launch_bounds__(256) k_hm_rows(int m, int p, const int* __rest
             }
         }
     }
-    if (r < nr) {
+    for (int g = 1; g < ng; ++g) {
+        __syncthreads();
+        if (grp == g && r < nr) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) sx[r * NB + c] = acc[c];
+        }
+        __syncthreads();
+        if (grp == 0 && r < nr) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) acc[c] = cadd(acc[c], sx[r * NB + c]);
+        }
+    }
+    if (grp == 0 && r < nr) {
         const int row = perm[rs + r];
 #pragma unroll
         for (int c = 0; c < NB; ++c)
@@ -614,14 +633,21 @@ void hm_apply(Ctx& c, int p, const cx<R>* X, int64_t ldx, cx<R>* Y, int64_t ldy,
         cx<R>* Yc = Y + (size_t)c0 * ldy;
         const int64_t tot = (int64_t)H.m * pc;
         k_hm_gather<R><<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 16), 256, 0, st>>>(H.m, pc, H.perm, Xc, ldx, xt);
+        const int rt = H.rows_threads, ng = std::max(1, std::min(4, 512 / rt));
         if (pc <= 8) {
+            const size_t sm = (size_t)std::max(kHmStage, rt) * 8 * sizeof(cx<R>);
+            if (sm > 48 * 1024)
+                VSIE_CUDA(cudaFuncSetAttribute(k_hm_rows<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             if (H.nlr) k_hm_vt<R, 8><<<H.nlr, 256, 0, st>>>(H.m, pc, H.lr, H.blk, H.kb, H.voff, H.toff, V, xt, t);
-            k_hm_rows<R, 8><<<H.nrl, H.rows_threads, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
-                                                  H.doff, D, U, H.toff, t, xt, Yc, ldy);
+            k_hm_rows<R, 8><<<H.nrl, rt * ng, sm, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
+                                                        H.doff, D, U, H.toff, t, xt, Yc, ldy, rt);
         } else {
+            const size_t sm = (size_t)std::max(kHmStage, rt) * 16 * sizeof(cx<R>);
+            if (sm > 48 * 1024)
+                VSIE_CUDA(cudaFuncSetAttribute(k_hm_rows<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             if (H.nlr) k_hm_vt<R, 16><<<H.nlr, 256, 0, st>>>(H.m, pc, H.lr, H.blk, H.kb, H.voff, H.toff, V, xt, t);
-            k_hm_rows<R, 16><<<H.nrl, H.rows_threads, 0, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
-                                                   H.doff, D, U, H.toff, t, xt, Yc, ldy);
+            k_hm_rows<R, 16><<<H.nrl, rt * ng, sm, st>>>(H.m, pc, H.perm, H.rl, H.eptr, H.eblk, H.eroff, H.blk, H.kb,
+                                                         H.doff, D, U, H.toff, t, xt, Yc, ldy, rt);
         }
         prof_count(c, H.nlr ? 3 : 2);
     }

@@ -86,7 +86,7 @@ static inline int nblk(int64_t n) { return (int)std::min<int64_t>((n + 255) / 25
 // step), all p right-hand sides, material voxels only.  G1 is n1 x r1
 // (column-major), a body column is the n1 voxels i1 of one (i2, i3).
 constexpr int kG1Cols = 8;    // columns per CTA, forward
-constexpr int kG1tCols = 32;  // columns per CTA, transposed
+constexpr int kG1tCols = 28;  // columns per CTA, transposed (r1 x 28 <= 256 outputs: one round for r1 <= 9)
 
 // y[j][i1 + n1 col] += sum_r G1[i1 + n1 r] t3[j][r + r1 col]   (mask[i1 + n1 col] != 0)
 template <typename R>
