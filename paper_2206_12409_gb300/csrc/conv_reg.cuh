@@ -448,21 +448,23 @@ __global__ void __launch_bounds__(ZStaged<R2, NL, SPLIT>::NT, ZStaged<R2, NL, SP
     const size_t oct = (size_t)a.Lh1 * a.Lh2 * a.Lh3;
     const size_t st3 = (size_t)a.Lh1 * a.Lh2;
     for (int i = threadIdx.x; i < L3; i += NT) tw[i] = a.tw3[i];
-    // spectrum tile: row r = c6 Lh3 + kk3, column l
-    for (int e = threadIdx.x; e < 6 * a.Lh3 * NL; e += NT) {
-        const int l = e % NL, r = e / NL;
-        const int c6 = r / a.Lh3, kk3 = r - c6 * a.Lh3;
-        const int k1g = k10 + l;
+    // spectrum tile: row r = c6 Lh3 + kk3, column l (each thread keeps one column;
+    // NT is a multiple of NL, so the loops need no runtime division)
+    static_assert(NT % NL == 0 && NT % (NL / 2) == 0, "thread count must tile the line columns");
+    {
+        const int l = threadIdx.x % NL, k1g = k10 + l;
         const int kk1 = k1g <= a.L1 / 2 ? k1g : a.L1 - k1g;
-        cpa8(sp + (size_t)srow_sw(r, NL) * NL + l, a.spec + c6 * oct + kk3 * st3 + (size_t)kk2 * a.Lh1 + kk1);
+        const C* sb = a.spec + (size_t)kk2 * a.Lh1 + kk1;
+        for (int c6 = 0; c6 < 6; ++c6)
+            for (int kk3 = threadIdx.x / NL; kk3 < a.Lh3; kk3 += NT / NL)
+                cpa8(sp + (size_t)srow_sw(c6 * a.Lh3 + kk3, NL) * NL + l, sb + c6 * oct + kk3 * st3);
     }
     auto prefetch = [&](int j) {
         const C* src = a.B + (size_t)j * 3 * cstride + (size_t)k2 * a.L1 + k10;
-        for (int e = threadIdx.x; e < 3 * a.n3 * (NL / 2); e += NT) {
-            const int part = e % (NL / 2), row = e / (NL / 2);   // row = comp n3 + n
-            const int comp = row / a.n3, n = row - comp * a.n3;
-            cpa16(pre + (size_t)row * NL + 2 * part, src + comp * cstride + (size_t)n * plane + 2 * part);
-        }
+        const int part = threadIdx.x % (NL / 2);
+        for (int comp = 0; comp < 3; ++comp)
+            for (int n = threadIdx.x / (NL / 2); n < a.n3; n += NT / (NL / 2))
+                cpa16(pre + (size_t)(comp * a.n3 + n) * NL + 2 * part, src + comp * cstride + (size_t)n * plane + 2 * part);
     };
     prefetch(0);
     cpa_commit();
