@@ -22,6 +22,7 @@ gmres     GMRES(m) and flexible GMRES (Sec. III.A)
 mie       Mie series for the field inside a homogeneous sphere (solver-level pin)
 rhs       plane-wave right-hand side of the hybrid system (Sec. II.A)
 ports     lumped loads and the Y, Z, S matrices of the ports (Sec. IV.B, V)
+tucker    Tucker (HOSVD) compression of the body block's Green generators (Sec. II.A)
 
 Parity status of each function is stated in its docstring; functions without an
 independent pin say "parity unpinned".
